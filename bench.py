@@ -1,0 +1,327 @@
+"""Benchmark: integrated reactor states per second for one global step.
+
+Workload: the seeded H2/O2-like mechanism (13 species, 27 reactions) on 2^20
+PaSR-like states (20 % near-equilibrium products, 80 % ignition-delay
+states, random order), one global step dt (default 1e-4 s; 1e-6 s is also
+reported), rtol 1e-6, atol 1e-10.  A step is one kin_integrate of the whole
+batch; inputs are restored from a pristine device copy and L2 is flushed
+(256 MiB write) before every timed step, outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank integrates its own copy of the workload (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "h2_mixed_2p20"
+METRIC = "integrated states/sec per global step (dt=1e-6, 1e-4 s) vs plain FP64 GPU Radau, equal error"
+RTOL, ATOL = 1e-6, 1e-10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--dt", type=float, default=1e-4)
+    p.add_argument("--layout", default="queue", choices=["plain", "queue"])
+    p.add_argument("--fp32", type=int, default=1, help="FP32 Newton matrices (1) or FP64 (0)")
+    p.add_argument("--n", type=int, default=0, help="states (0 = the workload's 2^20)")
+    p.add_argument("--no-extras", action="store_true", help="skip the comparison legs")
+    p.add_argument("--cpu-sample", type=int, default=2048)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic operation counts (FP64 / FP32 flops per event)
+# ---------------------------------------------------------------------------
+
+def op_model(mech):
+    """Flops of one right-hand side, Jacobian, factorisation pair and Newton
+    solve pair for this mechanism (transcendentals count as one flop)."""
+    ns, N = mech.ns, mech.ns
+    neff = [(int(np.sum(mech.eff[i] != 1.0)) if mech.rtype[i] else 0) for i in range(mech.nr)]
+    slots = [int(np.sum(mech.reac[i] >= 0) + np.sum(mech.prod[i] >= 0)) for i in range(mech.nr)]
+    f_rhs = 36 * ns + 3 * N
+    for i in range(mech.nr):
+        f_rhs += 20 + 2 * slots[i] + 2 * neff[i] + (45 if mech.rtype[i] == 2 else 0)
+    f_jac = f_rhs + 10 * N * N
+    for i in range(mech.nr):
+        f_jac += 12 + slots[i] * (4 * slots[i] + 4 * neff[i]) + (30 if mech.rtype[i] == 2 else 0)
+    f_lu = (2.0 / 3.0) * N ** 3 + (8.0 / 3.0) * N ** 3 + 3 * N * N   # real + complex + build
+    f_sol = 2 * N * N + 8 * N * N + 40 * N                           # both solves + transforms
+    f_err = 2 * N * N + 10 * N
+    return dict(rhs=f_rhs, jac=f_jac, lu=f_lu, sol=f_sol, err=f_err)
+
+
+def algorithmic_flops(tot, ops, fp32):
+    """FP64 and FP32 flops of one launch from the summed counters."""
+    f64 = tot["nfcn"] * ops["rhs"] + tot["njac"] * ops["jac"] + tot["naccpt"] * ops["err"]
+    lin = tot["ndec"] * ops["lu"] + tot["nsol"] * ops["sol"]
+    return (f64, lin) if fp32 else (f64 + lin, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1607_03884_gb300 import kin, synth
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    mech, st, _ = synth.workload(WORKLOAD, n=args.n or None)
+    n = st.n
+    mg = kin.Mechanism(mech)
+    Y0 = torch.from_numpy(st.Y).cuda()
+    T0 = torch.from_numpy(st.T).cuda()
+    P = torch.from_numpy(st.P).cuda()
+    Y, T = Y0.clone(), T0.clone()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    opt = dict(layout=args.layout, lu_fp32=bool(args.fp32))
+    ops = op_model(mech)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def one(dt, o, timed):
+        Y.copy_(Y0)
+        T.copy_(T0)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mg.integrate(Y, T, P, dt, RTOL, ATOL, stream=stream, **o)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    for _ in range(args.warmup):
+        one(args.dt, opt, False)
+    barrier()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    wall0 = time.perf_counter()
+    times = [one(args.dt, opt, True) for _ in range(args.steps)]
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    tot = mg.stats()
+    t_step = float(np.mean(times))
+    t_max = t_step
+    if dist is not None:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = n * world / t_max
+    f64, f32 = algorithmic_flops(tot, ops, bool(args.fp32))
+
+    out = {}
+    if rank == 0 and not args.no_extras:
+        # the plain FP64 one-state-per-thread kernel on the same workload
+        base_opt = dict(layout="plain", lu_fp32=False)
+        one(args.dt, base_opt, False)
+        tb = [one(args.dt, base_opt, True) for _ in range(max(1, min(args.steps, 2)))]
+        out["plain_fp64_states_per_s"] = n / float(np.mean(tb))
+        # dt = 1e-6 for both
+        other = 1e-6 if args.dt != 1e-6 else 1e-4
+        one(other, opt, False)
+        t_o = float(np.mean([one(other, opt, True) for _ in range(2)]))
+        one(other, base_opt, False)
+        t_ob = float(np.mean([one(other, base_opt, True) for _ in range(2)]))
+        out["per_dt"] = {str(args.dt): {"ours": value / world, "plain_fp64": out["plain_fp64_states_per_s"]},
+                         str(other): {"ours": n / t_o, "plain_fp64": n / t_ob}}
+        # end to end through the host-buffer entry (pinned buffers)
+        Yh = torch.from_numpy(st.Y.copy()).pin_memory()
+        Th = torch.from_numpy(st.T.copy()).pin_memory()
+        Ph = torch.from_numpy(st.P.copy()).pin_memory()
+        Yp = Yh.clone().pin_memory()
+        Tp = Th.clone().pin_memory()
+        mg.integrate_host(Yp, Tp, Ph, args.dt, RTOL, ATOL, stream=stream, **opt)
+        te = []
+        for _ in range(max(1, min(args.steps, 3))):
+            Yp.copy_(Yh)
+            Tp.copy_(Th)
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mg.integrate_host(Yp, Tp, Ph, args.dt, RTOL, ATOL, stream=stream, **opt)
+            te.append(time.perf_counter() - t0)
+        out["e2e"] = {"value": n / float(np.mean(te)), "unit": "states/s",
+                      "h2d_bytes_per_step": int(n * (mech.ns + 2) * 8),
+                      "d2h_bytes_per_step": int(n * (mech.ns + 1) * 8)}
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return dict(value=value, t_step=t_max, times=times, wall=wall, clocks=clocks, tot=tot,
+                f64=f64, f32=f32, n=n, mech=mech, st=st, extras=out)
+
+
+def cpu_baseline(sample, dt):
+    from oracle import oracle as O
+    from paper_1607_03884_gb300 import synth
+    mech, st, _ = synth.workload(WORKLOAD)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(st.n, size=sample, replace=False))
+    sub = st.subset(idx)
+    t0 = time.perf_counter()
+    O.integrate(mech, sub, dt, rtol=RTOL, atol=ATOL)
+    el = time.perf_counter() - t0
+    return {"value": sample / el, "unit": "states/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{sample} states drawn (seed 1) from the {WORKLOAD} workload, dt={dt:g}",
+            "seconds": el}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+# FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock).
+# The unit count is measured on this GB300 (dependent-FMA kernel on all SMs:
+# 1.198 TFLOP/s); FP32: 152 x 128 lanes x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reps = []
+        for _ in range(args.warmup + args.steps):
+            reps.append(cpu_baseline(max(64, args.cpu_sample // 4), args.dt))
+        vals = [r["value"] for r in reps[args.warmup:]]
+        v = float(np.mean(vals))
+        cb = dict(reps[-1])
+        cb["value"] = v
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": "states/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * cb["seconds"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dt": args.dt, "rtol": RTOL, "atol": ATOL,
+                       "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+    r = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    pk = peaks()
+    t = r["t_step"]
+    a64 = r["f64"] / t / 1e12
+    roof = {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": a64 / FP64_PEAK_TFLOPS, "traffic": None,
+            "pipe": "fp64", "kernel": f"k_integrate_{args.layout}",
+            "peak_source": "152 SMs x 2 FP64 FMA/clk x 2.07 GHz (unit count measured)",
+            "fp32_tflops": r["f32"] / t / 1e12}
+    cb = cpu_baseline(args.cpu_sample, args.dt) if not args.no_extras else None
+    ex = r["extras"]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": "states/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if args.fp32 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "states": r["n"], "species": r["mech"].ns,
+                   "reactions": r["mech"].nr, "dt": args.dt, "rtol": RTOL, "atol": ATOL,
+                   "layout": args.layout, "newton_matrices": "fp32" if args.fp32 else "fp64",
+                   "l2": "flushed (256 MiB write) and inputs restored before each timed step"},
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "e2e": ex.get("e2e"),
+        "gpu_launches": args.steps,
+        "clocks": r["clocks"],
+        "plain_fp64_states_per_s": ex.get("plain_fp64_states_per_s"),
+        "per_dt": ex.get("per_dt"),
+        "counters": {k: int(v) for k, v in r["tot"].items()},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * kin — batched Radau IIA integration of constant-pressure reactor states on
+ * NVIDIA GB300 (sm_103a).  C ABI of libkin.so.
+ *
+ * What is computed (Curtis, Niemeyer & Sung, "An investigation of GPU-based
+ * stiff chemical kinetics integration methods"): each state (T, P, Y) is an
+ * independent initial-value problem of the constant-pressure,
+ * mass-fraction-based reactor (Sec. 2.1), advanced over one global time step
+ * dt with the three-stage, fifth-order Radau IIA method, adaptive internal
+ * steps under atol/rtol and per-IVP Jacobian reuse (Sec. 2.1), with an
+ * analytical Jacobian or a CVODE-style finite-difference one (Sec. 2.1,
+ * Sec. 3.4).  Source terms: reversible Arrhenius, third-body and Troe
+ * falloff reactions, reverse rates from NASA-7 thermodynamics.
+ *
+ * Conventions for every entry point:
+ *   - Units are SI with kmol: T in K, P in Pa, W in kg/kmol, Arrhenius A in
+ *     (m^3/kmol)^(order-1)/s, activation temperatures Theta = Ea/R in K.
+ *   - States are stored species-major (structure of arrays): Y[k*n + i] is
+ *     the mass fraction of species k in state i; T[i], P[i].  All ns mass
+ *     fractions are stored; the last species is inert and, on output, equals
+ *     1 minus the sum of the others.
+ *   - "dev" pointers are CUDA device pointers owned by the caller; "host"
+ *     pointers are host memory owned by the caller.  The library owns the
+ *     mechanism tables, its workspace and its counters.
+ *   - Functions taking a stream are asynchronous on that stream (NULL = the
+ *     legacy default stream); results are valid after the stream
+ *     synchronises.  A kin_mech is used by one stream at a time.
+ *   - Errors: every function returns a kin_status.  Argument errors and CUDA
+ *     errors are reported at call time and leave outputs unspecified.
+ *     Per-state numerical failures are not call errors: they are written to
+ *     the optional status array, and the failed state keeps its last
+ *     accepted values (a failing IVP keeps its solution, Sec. 1).
+ */
+#ifndef KIN_H
+#define KIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KIN_OK = 0,
+  KIN_ERR_INVALID_ARG = 1,
+  KIN_ERR_CUDA = 2,
+  KIN_ERR_NOMEM = 3,
+  KIN_ERR_MECH = 4,
+  KIN_ERR_STATE_FAILED = 5,
+  KIN_ERR_UNSUPPORTED = 6
+} kin_status;
+
+/* per-state status codes written to the status array */
+enum {
+  KIN_STATE_OK = 0,
+  KIN_STATE_MAX_STEPS = 1,   /* internal step limit reached */
+  KIN_STATE_H_UNDERFLOW = 2, /* internal step below round-off of t */
+  KIN_STATE_SINGULAR = 3,    /* iteration matrix singular 5 times in a row */
+  KIN_STATE_NONFINITE = 4    /* non-finite right-hand side or Jacobian */
+};
+
+/* maximum number of species (N = ns unknowns per state) */
+#define KIN_MAX_SPECIES 64
+
+/* Mechanism description: plain host arrays, copied by kin_mech_create.
+ *   W     [ns]      molar masses
+ *   nasa  [ns*17]   T_low, T_mid, T_high, 7 coefficients for T < T_mid,
+ *                   7 for T >= T_mid (NASA-7: cp/R, h/RT, s/R polynomials)
+ *   reac  [nr*3]    species index of each reactant slot, -1 = empty slot
+ *                   (a species listed twice has coefficient 2)
+ *   prod  [nr*3]    same for products
+ *   arrh  [nr*3]    A, b, Theta of k = A T^b exp(-Theta/T) (k_inf for Troe)
+ *   rtype [nr]      0 elementary, 1 third body, 2 Troe falloff
+ *   eff   [nr*ns]   collision efficiencies (used by types 1 and 2; 1 = default)
+ *   fall  [nr*7]    type 2: k0 A, k0 b, k0 Theta, Troe a, T***, T*, T**
+ * The last species (ns-1) must take part in no reaction (it may collide). */
+typedef struct {
+  int32_t ns, nr;
+  const double *W;
+  const double *nasa;
+  const int32_t *reac;
+  const int32_t *prod;
+  const double *arrh;
+  const int32_t *rtype;
+  const double *eff;
+  const double *fall;
+} kin_mech_desc;
+
+typedef struct kin_mech kin_mech;
+
+/* Kernel layouts. */
+enum {
+  KIN_LAYOUT_PLAIN = 0, /* one state per thread, nested step/Newton loops: the
+                           paper's GPU organisation (Sec. 1, Sec. 3.3) */
+  KIN_LAYOUT_QUEUE = 1  /* one state per thread in a persistent launch: every
+                           loop trip evaluates one right-hand side per lane,
+                           and a lane whose state is done takes the next one
+                           from an atomic work queue (answers the warp
+                           divergence of Sec. 3.3) */
+};
+
+/* Integration options.  kin_options_default fills the defaults. */
+typedef struct {
+  int32_t layout;        /* KIN_LAYOUT_*                                   (1) */
+  int32_t lu_fp32;       /* 1: Jacobian storage, factorisation and solves of
+                            the Newton matrices in FP32 (rates, residuals,
+                            stage update, error estimate stay FP64)       (0) */
+  int32_t jac_fd;        /* 1: CVODE-style one-sided difference Jacobian   (0) */
+  int32_t max_steps;     /* internal step limit per state             (100000) */
+  int32_t nit;           /* Newton iterations per step                     (7) */
+  int32_t block;         /* threads per block; 0 = library choice          (0) */
+  int32_t grid_per_sm;   /* QUEUE: resident blocks per SM; 0 = occupancy   (0) */
+  int32_t transform_tol; /* 1: rtol' = 0.1 rtol^(2/3), atol' = rtol' atol/rtol (1) */
+  const double *h0;      /* dev [n] first internal step per state, or NULL  */
+  const double *z0;      /* dev [3*ns][n] first-step stage guesses, or NULL */
+  double *h_first;       /* dev [n] out: first accepted step, or NULL       */
+  double *z_first;       /* dev [3*ns][n] out: converged first-step stages  */
+} kin_options;
+
+/* Per-state counters written by kin_integrate_ex when counters != NULL:
+ * counters[c*n + i] for c in this order. */
+enum {
+  KIN_CNT_NSTEP = 0, KIN_CNT_NACCPT, KIN_CNT_NREJCT, KIN_CNT_NFCN, KIN_CNT_NJAC,
+  KIN_CNT_NDEC, KIN_CNT_NSOL, KIN_CNT_STATUS, KIN_NCOUNTERS
+};
+
+/* Fill *opt with the defaults shown above.  Returns KIN_ERR_INVALID_ARG for NULL. */
+int kin_options_default(kin_options *opt);
+
+/* Copy a mechanism description to the device and build its tables
+ * (Sec. 2.1: source terms and Jacobian of the chosen model).  *out receives a
+ * handle to free with kin_destroy.  Errors: KIN_ERR_INVALID_ARG (NULL or
+ * ns outside [2, KIN_MAX_SPECIES], nr < 1), KIN_ERR_MECH (a slot index out
+ * of range, an inert species that reacts, a non-positive molar mass or
+ * temperature bound), KIN_ERR_NOMEM / KIN_ERR_CUDA (device allocation). */
+int kin_mech_create(const kin_mech_desc *desc, kin_mech **out);
+
+/* Free a mechanism and its workspace.  NULL is ignored.  The caller must not
+ * have work in flight on the mechanism. */
+void kin_destroy(kin_mech *m);
+
+/* Advance n independent states over one global step dt (Sec. 2.1, Sec. 3):
+ * Y dev [ns][n] in/out, T dev [n] in/out, P dev [n] (constant).  Radau IIA
+ * with rtol/atol (the paper uses rtol 1e-6, atol 1e-10) and the default
+ * options.  n = 0 is a no-op.  Errors: KIN_ERR_INVALID_ARG for NULL
+ * pointers with n > 0, n < 0, dt <= 0 or non-positive tolerances;
+ * KIN_ERR_CUDA if a launch fails. */
+int kin_integrate(kin_mech *m, double *Y, double *T, const double *P, int64_t n, double dt,
+                  double rtol, double atol, void *stream);
+
+/* kin_integrate with options (NULL = defaults) and optional per-state
+ * outputs: status dev [n] (KIN_STATE_*), counters dev [KIN_NCOUNTERS][n]
+ * (statistics and the internal step counts d_i of Sec. 3.3). */
+int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double *P, int64_t n, double dt,
+                     double rtol, double atol, const kin_options *opt, int32_t *status,
+                     int32_t *counters, void *stream);
+
+/* The same integration from HOST buffers: the library copies the inputs to
+ * device buffers it owns, integrates, copies Y and T back and synchronises
+ * the stream before returning (the paper's timing includes these copies,
+ * Sec. 3).  Y host [ns][n], T host [n] in/out; P host [n]; status and
+ * counters host or NULL.  Device pointers inside opt are not allowed
+ * (KIN_ERR_INVALID_ARG).  Pinned host memory gives asynchronous copies. */
+int kin_integrate_host(kin_mech *m, double *Y, double *T, const double *P, int64_t n, double dt,
+                       double rtol, double atol, const kin_options *opt, int32_t *status,
+                       int32_t *counters, void *stream);
+
+/* Totals of the last kin_integrate* call on this mechanism, reduced on the
+ * device: out[0..6] = sums of the KIN_CNT_* counters 0..6, out[7] = number of
+ * failed states, out[8] = largest per-state step count.  Synchronises the
+ * mechanism's last stream.  Returns KIN_ERR_STATE_FAILED when out[7] > 0. */
+int kin_get_stats(kin_mech *m, int64_t *out);
+
+/* Source terms f(y) for n states (y = [T, Y_0..Y_{ns-2}], N = ns):
+ * y dev [N][n], P dev [n], f dev [N][n] out.  Unit-level entry of the
+ * right-hand side every Radau stage evaluates (Sec. 2.1). */
+int kin_rhs(kin_mech *m, const double *y, const double *P, int64_t n, double *f, void *stream);
+
+/* Jacobian df/dy for n states: J dev [N*N][n] out, entry (r, c) at
+ * J[(r*N + c)*n + i].  fd = 0: analytical (Sec. 2.1); fd = 1: the one-sided
+ * difference quotient with the CVODE increment rule, which also needs
+ * h (the internal step) and scal dev [N][n] (error weights 1/w). */
+int kin_jacobian(kin_mech *m, const double *y, const double *P, int64_t n, int32_t fd, double h,
+                 const double *scal, double *J, void *stream);
+
+/* Radau IIA constants the kernels use, computed by the library from closed
+ * forms (Hairer & Wanner IV.5, IV.8; the method of Sec. 2.1):
+ * out[0..2] c, [3..5] gamma, alpha, beta (eigenvalues of A^-1),
+ * [6..14] T row-major, [15..23] T^-1, [24..26] error weights d_i
+ * (the estimate is (gamma/h I - J)^-1 (f0 + sum d_i z_i / h)).  len >= 27.
+ * Needs no GPU. */
+int kin_radau_constants(double *out, int32_t len);
+
+/* Message for a kin_status. */
+const char *kin_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,173 @@
+// Integration kernels (PLAIN and QUEUE layouts) and their launch helper,
+// instantiated per (species capacity, matrix precision) in the kin_tu_*.cu
+// translation units so that the library compiles in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/kin.h"
+#include "kin_radau.cuh"
+
+namespace kin {
+
+#define KIN_CUDA_TRY(expr)                                                    \
+  do {                                                                        \
+    cudaError_t e_ = (expr);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      (void)cudaGetLastError();                                               \
+      return e_ == cudaErrorMemoryAllocation ? KIN_ERR_NOMEM : KIN_ERR_CUDA; \
+    }                                                                         \
+  } while (0)
+
+inline size_t smem_bytes(const MechLayout &L) {
+  return sizeof(double) * (size_t)L.nd + sizeof(int) * (size_t)L.ni;
+}
+
+struct KernelArgs {
+  MechLayout L;
+  const double *tab;
+  const int *itab;
+  double *Y, *T;
+  const double *P;
+  int32_t *status, *counters;
+  unsigned long long *totals;
+  RadauParams rp;
+};
+
+template <int MAXN, typename LT>
+__device__ void load_state(Work<MAXN, LT> &w, const KernelArgs &a, int N, int64_t i) {
+  const int64_t n = a.rp.n;
+  w.y[0] = a.T[i];
+  for (int k = 0; k < N - 1; ++k) w.y[1 + k] = a.Y[(int64_t)k * n + i];
+}
+
+template <int MAXN, typename LT>
+__device__ void store_state(const Work<MAXN, LT> &w, const StepState &s, const KernelArgs &a,
+                            int N, int64_t i) {
+  const int64_t n = a.rp.n;
+  a.T[i] = w.y[0];
+  double sum = 0.0;
+  for (int k = 0; k < N - 1; ++k) {
+    a.Y[(int64_t)k * n + i] = w.y[1 + k];
+    sum += w.y[1 + k];
+  }
+  a.Y[(int64_t)(N - 1) * n + i] = 1.0 - sum;
+  if (a.status) a.status[i] = s.status;
+  if (a.counters) {
+    const int32_t c[8] = {s.nstep, s.naccpt, s.nrejct, s.nfcn, s.njac, s.ndec, s.nsol, s.status};
+    for (int q = 0; q < 8; ++q) a.counters[(int64_t)q * n + i] = c[q];
+  }
+  const unsigned long long c7[7] = {(unsigned long long)s.nstep, (unsigned long long)s.naccpt,
+                                    (unsigned long long)s.nrejct, (unsigned long long)s.nfcn,
+                                    (unsigned long long)s.njac, (unsigned long long)s.ndec,
+                                    (unsigned long long)s.nsol};
+  for (int q = 0; q < 7; ++q) atomicAdd(a.totals + q, c7[q]);
+  if (s.status) atomicAdd(a.totals + 7, 1ull);
+  atomicMax(a.totals + 8, (unsigned long long)s.nstep);
+}
+
+template <int MAXN, typename LT, bool FDJ>
+__global__ void __launch_bounds__(64) k_integrate_plain(KernelArgs a) {
+  extern __shared__ double smem[];
+  const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.rp.n) return;
+  Work<MAXN, LT> w;
+  StepState s;
+  const int N = m.ns;
+  load_state(w, a, N, i);
+  integrate_plain<MAXN, LT, FDJ>(m, a.P[i], w, s, a.rp, i);
+  store_state(w, s, a, N, i);
+}
+
+template <int MAXN, typename LT, bool FDJ>
+__global__ void __launch_bounds__(64) k_integrate_queue(KernelArgs a) {
+  extern __shared__ double smem[];
+  const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
+  const int N = m.ns;
+  const int64_t n = a.rp.n;
+  unsigned long long *queue = a.totals + 9;
+  Work<MAXN, LT> w;
+  StepState s;
+  Machine<MAXN, LT, FDJ> mc;
+  int64_t idx = -1;
+  double P = 0.0;
+  // Each trip: (re)fill, one right-hand side, bookkeeping.  The trip count is
+  // bounded: every state takes at most max_steps steps of at most nit + 2 + N
+  // evaluations each, plus a constant; the guard stops a runaway lane.
+  for (long long trip = 0;; ++trip) {
+    if (idx < 0) {
+      const unsigned long long t = atomicAdd(queue, 1ull);
+      if ((int64_t)t >= n) break;
+      idx = (int64_t)t;
+      P = a.P[idx];
+      load_state(w, a, N, idx);
+      init_state<MAXN, LT>(s);
+      for (int k = 0; k < N; ++k) w.u[k] = w.y[k];
+      mc.phase = PH_F0_INIT;
+      trip = 0;
+    }
+    const int rc = rhs<MAXN>(m, P, w.u, w.fu, w.cs);
+    bool more = mc.advance(m, P, w, s, a.rp, idx, rc);
+    if (more && trip > (long long)a.rp.max_steps * (a.rp.nit * 3 + 4 + N) + 16) {
+      s.status = 1;
+      more = false;
+    }
+    if (!more) {
+      store_state(w, s, a, N, idx);
+      idx = -1;
+    }
+  }
+}
+
+template <int MAXN, typename LT, bool FDJ>
+int launch_t(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms) {
+  const size_t sm = smem_bytes(a.L);
+  const int block = o.block > 0 ? o.block : 64;
+  if (block > 64 || block % 32) return KIN_ERR_INVALID_ARG;
+  if (o.layout == KIN_LAYOUT_PLAIN) {
+    auto kern = k_integrate_plain<MAXN, LT, FDJ>;
+    KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int64_t grid = (a.rp.n + block - 1) / block;
+    kern<<<(unsigned)grid, block, sm, st>>>(a);
+  } else {
+    auto kern = k_integrate_queue<MAXN, LT, FDJ>;
+    KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = o.grid_per_sm;
+    if (per_sm <= 0) {
+      KIN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm));
+      if (per_sm < 1) per_sm = 1;
+    }
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t need = (a.rp.n + block - 1) / block;
+    if (grid > need) grid = need;
+    kern<<<(unsigned)grid, block, sm, st>>>(a);
+  }
+  KIN_CUDA_TRY(cudaGetLastError());
+  return KIN_OK;
+}
+
+
+// Per-TU entry points: launch for one (MAXN, LT) pair and upload this TU's
+// copy of the Radau constants.
+#define KIN_DEFINE_TU(NAME, MAXN, LT)                                                   \
+  int kin_launch_##NAME(const KernelArgs &a, const kin_options &o, cudaStream_t st,    \
+                        int sms) {                                                     \
+    return o.jac_fd ? launch_t<MAXN, LT, true>(a, o, st, sms)                          \
+                    : launch_t<MAXN, LT, false>(a, o, st, sms);                        \
+  }                                                                                    \
+  int kin_consts_##NAME(const RadauConst &rc) {                                        \
+    KIN_CUDA_TRY(cudaMemcpyToSymbol(RC, &rc, sizeof rc));                              \
+    return KIN_OK;                                                                     \
+  }
+
+#define KIN_DECLARE_TU(NAME)                                                            \
+  int kin_launch_##NAME(const KernelArgs &a, const kin_options &o, cudaStream_t st,    \
+                        int sms);                                                      \
+  int kin_consts_##NAME(const RadauConst &rc);
+
+KIN_DECLARE_TU(16d)
+KIN_DECLARE_TU(16f)
+KIN_DECLARE_TU(64d)
+KIN_DECLARE_TU(64f)
+
+}  // namespace kin

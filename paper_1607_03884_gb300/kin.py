@@ -1,0 +1,212 @@
+"""ctypes binding of libkin (include/kin.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors / numpy arrays to pointers and C structs.  There is no CPU fallback:
+if libkin.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkin.so")
+
+KIN_OK, KIN_ERR_INVALID_ARG, KIN_ERR_CUDA, KIN_ERR_NOMEM, KIN_ERR_MECH = 0, 1, 2, 3, 4
+KIN_ERR_STATE_FAILED, KIN_ERR_UNSUPPORTED = 5, 6
+LAYOUT_PLAIN, LAYOUT_QUEUE = 0, 1
+COUNTER_NAMES = ("nstep", "naccpt", "nrejct", "nfcn", "njac", "ndec", "nsol", "status")
+MAX_SPECIES = 64
+
+# every symbol include/kin.h declares
+EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integrate",
+           "kin_integrate_ex", "kin_integrate_host", "kin_get_stats", "kin_rhs",
+           "kin_jacobian", "kin_radau_constants", "kin_status_string")
+
+
+class KinError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = _lib.kin_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} (status {code})" if what else msg)
+
+
+class MechDesc(C.Structure):
+    _fields_ = [("ns", C.c_int32), ("nr", C.c_int32), ("W", C.c_void_p), ("nasa", C.c_void_p),
+                ("reac", C.c_void_p), ("prod", C.c_void_p), ("arrh", C.c_void_p),
+                ("rtype", C.c_void_p), ("eff", C.c_void_p), ("fall", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("layout", C.c_int32), ("lu_fp32", C.c_int32), ("jac_fd", C.c_int32),
+                ("max_steps", C.c_int32), ("nit", C.c_int32), ("block", C.c_int32),
+                ("grid_per_sm", C.c_int32), ("transform_tol", C.c_int32),
+                ("h0", C.c_void_p), ("z0", C.c_void_p), ("h_first", C.c_void_p),
+                ("z_first", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libkin.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            if not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libkin.so not found at {LIB_PATH}")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+            L.kin_options_default.argtypes = [vp]
+            L.kin_mech_create.argtypes = [vp, C.POINTER(vp)]
+            L.kin_destroy.argtypes = [vp]
+            L.kin_destroy.restype = None
+            L.kin_integrate.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp]
+            L.kin_integrate_ex.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp, vp, vp]
+            L.kin_integrate_host.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp, vp, vp]
+            L.kin_get_stats.argtypes = [vp, vp]
+            L.kin_rhs.argtypes = [vp, vp, vp, i64, vp, vp]
+            L.kin_jacobian.argtypes = [vp, vp, vp, i64, i32, d, vp, vp, vp]
+            L.kin_radau_constants.argtypes = [vp, i32]
+            L.kin_status_string.argtypes = [C.c_int]
+            L.kin_status_string.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != KIN_OK:
+        raise KinError(rc, what)
+
+
+def _ptr(t):
+    """Device/host pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7, block=0,
+            grid_per_sm=0, transform_tol=True, h0=None, z0=None, h_first=None, z_first=None):
+    o = Options()
+    _check(lib().kin_options_default(C.byref(o)), "kin_options_default")
+    o.layout = {"plain": LAYOUT_PLAIN, "queue": LAYOUT_QUEUE}[layout] if isinstance(layout, str) \
+        else int(layout)
+    o.lu_fp32 = int(bool(lu_fp32))
+    o.jac_fd = int(bool(jac_fd))
+    o.max_steps = int(max_steps)
+    o.nit = int(nit)
+    o.block = int(block)
+    o.grid_per_sm = int(grid_per_sm)
+    o.transform_tol = int(bool(transform_tol))
+    o.h0, o.z0, o.h_first, o.z_first = _ptr(h0), _ptr(z0), _ptr(h_first), _ptr(z_first)
+    return o
+
+
+class Mechanism:
+    """A mechanism uploaded to the current CUDA device (kin_mech_create)."""
+
+    def __init__(self, mech):
+        self.ns, self.nr = int(mech.ns), int(mech.nr)
+        arrs = dict(
+            W=np.ascontiguousarray(mech.W, np.float64),
+            nasa=np.ascontiguousarray(mech.nasa, np.float64),
+            reac=np.ascontiguousarray(mech.reac, np.int32),
+            prod=np.ascontiguousarray(mech.prod, np.int32),
+            arrh=np.ascontiguousarray(mech.arrh, np.float64),
+            rtype=np.ascontiguousarray(mech.rtype, np.int32),
+            eff=np.ascontiguousarray(mech.eff, np.float64),
+            fall=np.ascontiguousarray(mech.fall, np.float64))
+        d = MechDesc(self.ns, self.nr, *(arrs[k].ctypes.data for k in
+                                          ("W", "nasa", "reac", "prod", "arrh", "rtype", "eff",
+                                           "fall")))
+        h = C.c_void_p()
+        _check(lib().kin_mech_create(C.byref(d), C.byref(h)), "kin_mech_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("mechanism destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.kin_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- integration --------------------------------------------------------
+    def integrate(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, status=None, counters=None,
+                  stream=None, **opt):
+        """Advance device tensors Y [ns, n], T [n] in place over dt (kin_integrate_ex)."""
+        n = int(T.shape[0])
+        o = options(**opt)
+        rc = lib().kin_integrate_ex(self.handle, _ptr(Y), _ptr(T), _ptr(P), n, float(dt),
+                                    float(rtol), float(atol), C.byref(o), _ptr(status),
+                                    _ptr(counters), _stream(stream))
+        _check(rc, "kin_integrate_ex")
+
+    def integrate_default(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, stream=None):
+        """kin_integrate: the default options."""
+        n = int(T.shape[0])
+        _check(lib().kin_integrate(self.handle, _ptr(Y), _ptr(T), _ptr(P), n, float(dt),
+                                   float(rtol), float(atol), _stream(stream)), "kin_integrate")
+
+    def integrate_host(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, status=None, counters=None,
+                       stream=None, **opt):
+        """Advance host arrays (numpy or CPU tensors) in place (kin_integrate_host)."""
+        n = int(T.shape[0])
+        o = options(**opt)
+        rc = lib().kin_integrate_host(self.handle, _ptr(Y), _ptr(T), _ptr(P), n, float(dt),
+                                      float(rtol), float(atol), C.byref(o), _ptr(status),
+                                      _ptr(counters), _stream(stream) if stream is not None else None)
+        _check(rc, "kin_integrate_host")
+
+    def stats(self):
+        """Totals of the last integration (kin_get_stats)."""
+        out = np.zeros(9, dtype=np.int64)
+        rc = lib().kin_get_stats(self.handle, out.ctypes.data)
+        if rc not in (KIN_OK, KIN_ERR_STATE_FAILED):
+            _check(rc, "kin_get_stats")
+        keys = list(COUNTER_NAMES[:7]) + ["failed", "max_steps_state"]
+        return dict(zip(keys, out.tolist()))
+
+    # -- unit-level entries ---------------------------------------------------
+    def rhs(self, y, P, f, stream=None):
+        n = int(P.shape[0])
+        _check(lib().kin_rhs(self.handle, _ptr(y), _ptr(P), n, _ptr(f), _stream(stream)), "kin_rhs")
+
+    def jacobian(self, y, P, J, fd=False, h=0.0, scal=None, stream=None):
+        n = int(P.shape[0])
+        _check(lib().kin_jacobian(self.handle, _ptr(y), _ptr(P), n, int(bool(fd)), float(h),
+                                  _ptr(scal), _ptr(J), _stream(stream)), "kin_jacobian")
+
+
+def radau_constants():
+    """The library's Radau IIA constants (kin_radau_constants): dict of arrays."""
+    out = np.zeros(27)
+    _check(lib().kin_radau_constants(out.ctypes.data, 27), "kin_radau_constants")
+    return dict(c=out[0:3], gamma=out[3], alpha=out[4], beta=out[5],
+                T=out[6:15].reshape(3, 3), TI=out[15:24].reshape(3, 3), d=out[24:27])
