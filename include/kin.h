@@ -93,10 +93,10 @@ enum {
   KIN_LAYOUT_PLAIN = 0, /* one state per thread, nested step/Newton loops: the
                            paper's GPU organisation (Sec. 1, Sec. 3.3) */
   KIN_LAYOUT_QUEUE = 1  /* one state per thread in a persistent launch: every
-                           loop trip evaluates one right-hand side per lane,
-                           and a lane whose state is done takes the next one
-                           from an atomic work queue (answers the warp
-                           divergence of Sec. 3.3) */
+                           loop trip is one step attempt per lane, and a lane
+                           whose state is done takes the next one from an
+                           atomic work queue (answers the warp divergence of
+                           Sec. 3.3: no lane waits for the slowest state) */
 };
 
 /* Integration options.  kin_options_default fills the defaults. */
@@ -182,6 +182,12 @@ int kin_rhs(kin_mech *m, const double *y, const double *P, int64_t n, double *f,
  * h (the internal step) and scal dev [N][n] (error weights 1/w). */
 int kin_jacobian(kin_mech *m, const double *y, const double *P, int64_t n, int32_t fd, double h,
                  const double *scal, double *J, void *stream);
+
+/* The exponential the rate kernels use (Tang's table-driven method, accurate
+ * to about 1 ulp for |x| <= 700, the library exp beyond): y[i] = exp(x[i]) for
+ * x, y dev [n].  Unit-level entry for testing; needs a mechanism only for
+ * its staged 2^(j/128) table. */
+int kin_exp(kin_mech *m, const double *x, double *y, int64_t n, void *stream);
 
 /* Radau IIA constants the kernels use, computed by the library from closed
  * forms (Hairer & Wanner IV.5, IV.8; the method of Sec. 2.1):

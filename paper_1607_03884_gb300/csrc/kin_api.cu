@@ -4,9 +4,9 @@
 // Radau IIA (Sec. 2.1 of Curtis, Niemeyer & Sung).  Two launch layouts:
 //   PLAIN  one thread per state, grid covers n (the paper's organisation);
 //   QUEUE  a persistent grid sized from the occupancy calculator; each lane
-//          pops state indices from an atomic counter and runs the one-RHS-
-//          per-trip state machine (kin_radau.cuh), so finished lanes never
-//          wait for the slowest lane of their warp (Sec. 3.3).
+//          attempts one step per loop trip and pops the next state index from
+//          an atomic counter when its state is finished, so finished lanes
+//          never wait for the slowest lane of their warp (Sec. 3.3).
 // Mechanism tables are staged into shared memory per CTA.
 #include <cuda_runtime.h>
 
@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/kin.h"
+#include "kin_internal.h"
 #include "kin_kernels.cuh"
 
 using namespace kin;
@@ -109,7 +110,7 @@ static RadauConst radau_constants_host() {
 static std::mutex g_const_mu;
 static bool g_const_done[64];
 
-static int ensure_constants(int dev) {
+int kin::ensure_constants(int dev) {
   std::lock_guard<std::mutex> lk(g_const_mu);
   if (dev < 0 || dev >= 64) return KIN_ERR_CUDA;
   if (g_const_done[dev]) return KIN_OK;
@@ -132,8 +133,9 @@ __global__ void k_rhs(MechLayout L, const double *tab, const int *itab, const do
   const int N = m.ns;
   double yy[MAXN], ff[MAXN];
   ChemScratch<MAXN> cs;
+  JacScratch<MAXN, double> js;
   for (int k = 0; k < N; ++k) yy[k] = y[(int64_t)k * n + i];
-  rhs<MAXN>(m, P[i], yy, ff, cs);
+  rhs<MAXN, double>(m, P[i], yy, ff, cs, js);
   for (int k = 0; k < N; ++k) f[(int64_t)k * n + i] = ff[k];
 }
 
@@ -149,23 +151,31 @@ __global__ void k_jac(MechLayout L, const double *tab, const int *itab, const do
   double yy[MAXN], f0[MAXN], sc[MAXN], u[MAXN], fu[MAXN];
   double J[MAXN * MAXN];
   ChemScratch<MAXN> cs;
-  JacScratch<MAXN> js;
+  JacScratch<MAXN, double> js;
   for (int k = 0; k < N; ++k) yy[k] = y[(int64_t)k * n + i];
   if (!fd) {
-    jac_analytic<MAXN>(m, P[i], yy, J, cs, js);
+    chem_eval<MAXN, double>(m, P[i], yy, f0, J, true, cs, js);
   } else {
     for (int k = 0; k < N; ++k) sc[k] = scal[(int64_t)k * n + i];
-    rhs<MAXN>(m, P[i], yy, f0, cs);
+    rhs<MAXN, double>(m, P[i], yy, f0, cs, js);
     double mininc = 0.0;
     for (int j = 0; j < N; ++j) {
       const double inc = fd_increment(N, yy, f0, sc, h, j, mininc, j == 0);
       for (int k = 0; k < N; ++k) u[k] = yy[k];
       u[j] = yy[j] + inc;
-      rhs<MAXN>(m, P[i], u, fu, cs);
+      rhs<MAXN, double>(m, P[i], u, fu, cs, js);
       for (int k = 0; k < N; ++k) J[k * N + j] = (fu[k] - f0[k]) / inc;
     }
   }
   for (int q = 0; q < N * N; ++q) Jout[(int64_t)q * n + i] = J[q];
+}
+
+__global__ void k_exp(const double *tab, const double *x, double *y, int64_t n) {
+  __shared__ double t[EXP_TAB];
+  for (int j = threadIdx.x; j < EXP_TAB; j += blockDim.x) t[j] = tab[j];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = kexp(x[i], t);
 }
 
 // ---------------------------------------------------------------------------
@@ -213,9 +223,10 @@ extern "C" int kin_radau_constants(double *out, int32_t len) {
   return KIN_OK;
 }
 
-extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
-  if (!d || !out) return KIN_ERR_INVALID_ARG;
-  *out = nullptr;
+// Validate a mechanism description and build its device tables on the host.
+int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double> &dt,
+                      std::vector<int> &it) {
+  if (!d) return KIN_ERR_INVALID_ARG;
   const int ns = d->ns, nr = d->nr;
   if (ns < 2 || ns > KIN_MAX_SPECIES || nr < 1) return KIN_ERR_INVALID_ARG;
   if (!d->W || !d->nasa || !d->reac || !d->prod || !d->arrh || !d->rtype || !d->eff || !d->fall)
@@ -248,7 +259,7 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
     if (t == 2 && !(d->fall[7 * i] > 0.0 && d->fall[7 * i + 4] > 0.0 && d->fall[7 * i + 5] > 0.0))
       return KIN_ERR_MECH;
   }
-  MechLayout L{};
+  L = MechLayout{};
   L.ns = ns;
   L.nr = nr;
   L.neff = neff;
@@ -264,6 +275,7 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
   L.dTh = o; o += nr;
   L.dtroe = o; o += NTROE * (ntroe > 0 ? ntroe : 1);
   L.deff = o; o += (neff > 0 ? neff : 1);
+  L.dexp = o; o += EXP_TAB;
   L.nd = o;
   int q = 0;
   L.islot = q; q += 6 * nr;
@@ -272,8 +284,8 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
   L.itroe = q;
   L.ieffsp = q; q += (neff > 0 ? neff : 1);
   L.ni = q;
-  std::vector<double> dt(L.nd, 0.0);
-  std::vector<int> it(L.ni, 0);
+  dt.assign(L.nd, 0.0);
+  it.assign(L.ni, 0);
   for (int k = 0; k < ns; ++k) {
     dt[L.dW + k] = d->W[k];
     dt[L.dinvW + k] = 1.0 / d->W[k];
@@ -291,6 +303,8 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
       s[5] = a[6];
     }
   }
+  // 2^(j/128), rounded to double, for the table-driven exponential
+  for (int j = 0; j < EXP_TAB; ++j) dt[L.dexp + j] = (double)exp2l((long double)j / EXP_TAB);
   int e = 0, tr = 0;
   for (int i = 0; i < nr; ++i) {
     dt[L.dlnA + i] = std::log(d->arrh[3 * i]);
@@ -332,6 +346,17 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
     it[L.imeta + i] = t | (nre << 2) | (npr << 4) | (ne << 8) | (troe_idx << 16);
   }
   if (smem_bytes(L) > 200 * 1024) return KIN_ERR_UNSUPPORTED;
+  return KIN_OK;
+}
+
+extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
+  if (!d || !out) return KIN_ERR_INVALID_ARG;
+  *out = nullptr;
+  MechLayout L;
+  std::vector<double> dt;
+  std::vector<int> it;
+  int brc = build_tables(d, L, dt, it);
+  if (brc) return brc;
   int dev = 0;
   KIN_CUDA_TRY(cudaGetDevice(&dev));
   int rc = ensure_constants(dev);
@@ -372,8 +397,8 @@ extern "C" void kin_destroy(kin_mech *m) {
   delete m;
 }
 
-static int launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t st,
-                           int sms) {
+int kin::launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t st,
+                         int sms) {
   if (a.L.ns <= 16) return o.lu_fp32 ? kin_launch_16f(a, o, st, sms) : kin_launch_16d(a, o, st, sms);
   return o.lu_fp32 ? kin_launch_64f(a, o, st, sms) : kin_launch_64d(a, o, st, sms);
 }
@@ -529,6 +554,16 @@ extern "C" int kin_jacobian(kin_mech *m, const double *y, const double *P, int64
     KIN_CUDA_TRY(cudaFuncSetAttribute(k_jac<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_jac<64><<<grid, block, sm, st>>>(m->L, m->d_tab, m->d_itab, y, P, n, fd, h, scal, J);
   }
+  KIN_CUDA_TRY(cudaGetLastError());
+  return KIN_OK;
+}
+
+extern "C" int kin_exp(kin_mech *m, const double *x, double *y, int64_t n, void *stream) {
+  if (!m || n < 0 || (n > 0 && (!x || !y))) return KIN_ERR_INVALID_ARG;
+  if (n == 0) return KIN_OK;
+  const int block = 256;
+  k_exp<<<(unsigned)((n + block - 1) / block), block, 0, (cudaStream_t)stream>>>(
+      m->d_tab + m->L.dexp, x, y, n);
   KIN_CUDA_TRY(cudaGetLastError());
   return KIN_OK;
 }

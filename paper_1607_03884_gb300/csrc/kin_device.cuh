@@ -29,7 +29,7 @@ struct MechLayout {
   int ns, nr, neff;
   int nd, ni;  // table sizes in doubles / ints
   // double-table offsets
-  int dW, dinvW, dTmid, dcp, dh, ds, dlnA, db, dTh, dtroe, deff;
+  int dW, dinvW, dTmid, dcp, dh, ds, dlnA, db, dTh, dtroe, deff, dexp;
   // int-table offsets
   int islot, imeta, ieff0, itroe, ieffsp;
 };
@@ -52,7 +52,7 @@ __device__ __forceinline__ int meta_troe(int w) { return w >> 16; }
 
 struct MechView {
   int ns, nr;
-  const double *W, *invW, *Tmid, *cp, *h, *s, *lnA, *b, *Th, *troe, *eff;
+  const double *W, *invW, *Tmid, *cp, *h, *s, *lnA, *b, *Th, *troe, *eff, *etab;
   const int *slot, *meta, *eff0, *effsp;
 };
 
@@ -71,6 +71,7 @@ __device__ __forceinline__ MechView make_view(const MechLayout &L, const double 
   v.Th = d + L.dTh;
   v.troe = d + L.dtroe;
   v.eff = d + L.deff;
+  v.etab = d + L.dexp;
   v.slot = i + L.islot;
   v.meta = i + L.imeta;
   v.eff0 = i + L.ieff0;
@@ -155,22 +156,78 @@ __device__ __forceinline__ TroeOut troe_factor(const double *tp, double T, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Right-hand side f(y).  Scratch arrays (MAXN each): C, g, hs, wd.
-// Returns 0, or KIN_STATE_NONFINITE (4) if any output is not finite.
+// Exponential for the rate expressions: Tang's table-driven method
+// (ACM TOMS 15, 1989).  exp(x) = 2^m 2^(j/128) exp(r) with N = round(128 x /
+// ln 2), j = N mod 128, m = N div 128, r = x - N ln2/128 (|r| <= ln2/256,
+// computed with ln2/128 split into a 29-bit head, so N*head is exact, and a
+// tail); exp(r) = 1 + r + r^2/2 + r^3/6 + r^4/24 + r^5/120 (truncation
+// below 6e-19).  The 128 values 2^(j/128) are rounded doubles computed by the
+// host and staged in shared memory.  Valid for |x| <= 700 (the result stays a
+// normal number); outside that range the library exp() is used.
+// ---------------------------------------------------------------------------
+constexpr int EXP_TAB = 128;
+
+__device__ __forceinline__ double kexp(double x, const double *tab) {
+  if (!(fabs(x) <= 700.0)) return exp(x);
+  const double inv = 0x1.71547652b82fep+7;    // 128 / ln 2
+  const double hi = 0x1.62e42ff000000p-8;     // ln2/128, 29 significant bits
+  const double lo = -0x1.718432a1b0e26p-42;   // ln2/128 - hi
+  const double shifter = 0x1.8p52;            // 1.5 * 2^52: rounds to an integer
+  double kd = fma(x, inv, shifter);
+  const int N = (int)(unsigned)__double2loint(kd);
+  kd -= shifter;
+  double r = fma(-kd, hi, x);
+  r = fma(-kd, lo, r);
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  q = fma(q, r, 1.0);
+  const double p = q * r;                     // exp(r) - 1
+  const double tj = tab[N & (EXP_TAB - 1)];
+  const double v = fma(tj, p, tj);
+  const long long m = (long long)(N >> 7);     // floor division (arithmetic shift)
+  return __longlong_as_double(__double_as_longlong(v) + (m << 52));
+}
+
+// ---------------------------------------------------------------------------
+// Source terms and (optionally) the analytical Jacobian at one point.
+//
+// f(y): thermo per species, then per reaction kf = exp(lnA + b lnT - Theta/T),
+// Kc from the Gibbs energies, kr = kf exp(-ln Kc), q = phi (kf prod C' -
+// kr prod C''), wdot scattered to the species, dY/dt = W wdot/rho and
+// dT/dt = -sum H wdot / (rho cp).  Rates are always FP64.
+//
+// J = df/dy (row-major N x N in the matrix type JT) reuses the same rates and
+// is assembled from the sparse reaction structure:
+//   dq/dY_j = (rho/W_j) D_j - (rho/W_in) D_in - (m_j/S) sigma',
+//   D_k = dq/dC_k without the uniform [M] part (that part multiplies
+//   d(sum C)/dY_j = 0 at fixed T, P), m_j = 1/W_j - 1/W_in,
+//   dq/dT = dq/dT|_C - sigma/T, sigma = sum_k dq/dC_k C_k,
+// then dY_k/dt = W_k wdot_k/rho and dT/dt = -sum H_k wdot_k/(rho cp) by the
+// product and quotient rules.  Per-reaction scalars are formed in FP64 and
+// the assembly arithmetic runs in JT (FP32 when the Newton matrices are FP32).
+// Returns 0, or 4 (KIN_STATE_NONFINITE) for a non-finite f or J.
 // ---------------------------------------------------------------------------
 template <int MAXN>
 struct ChemScratch {
   double C[MAXN], g[MAXN], hs[MAXN], cpk[MAXN], wd[MAXN];
 };
 
-template <int MAXN>
-__device__ __noinline__ int rhs(const MechView &m, double P, const double *y, double *f,
-                   ChemScratch<MAXN> &w) {
-  const int ns = m.ns, in = ns - 1;
+template <int MAXN, typename JT>
+struct JacScratch {
+  JT A[MAXN], B[MAXN], Tc[MAXN], mj[MAXN], Cj[MAXN], rW[MAXN];
+  double dcp[MAXN];
+};
+
+template <int MAXN, typename JT>
+__device__ __noinline__ int chem_eval(const MechView &m, double P, const double *y,
+                                      double *f, JT *J, bool wantJ, ChemScratch<MAXN> &w,
+                                      JacScratch<MAXN, JT> &x) {
+  const int ns = m.ns, in = ns - 1, N = ns;
   const double T = y[0];
   double sumY = 0.0, S = 0.0;
   for (int k = 0; k < in; ++k) {
-    double Yk = y[1 + k];
+    const double Yk = y[1 + k];
     sumY += Yk;
     S += Yk * m.invW[k];
   }
@@ -178,124 +235,41 @@ __device__ __noinline__ int rhs(const MechView &m, double P, const double *y, do
   S += Yin * m.invW[in];
   const double rho = P / (RU * T * S);
   const double logT = log(T), invT = 1.0 / T;
-  double cpm = 0.0;
-  for (int k = 0; k < ns; ++k) {
-    double Yk = (k < in) ? y[1 + k] : Yin;
-    w.C[k] = rho * Yk * m.invW[k];
-    int r = range_of(m, k, T);
-    double cp = poly_cp(m.cp + (2 * k + r) * NCP, T);
-    double h = poly_h(m.h + (2 * k + r) * NH, T, invT);
-    double s = poly_s(m.s + (2 * k + r) * NS, T, logT);
-    w.g[k] = s - h;
-    w.hs[k] = h;
-    cpm += Yk * cp * m.invW[k];
-    w.wd[k] = 0.0;
-  }
-  const double Ctot = rho * S;
-  const double lnPf = log(PATM / RU) - logT;
-  for (int i = 0; i < m.nr; ++i) {
-    const int meta = m.meta[i];
-    const int *sl = m.slot + 6 * i;
-    double kf = exp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT);
-    int nre = meta_nreac(meta), npr = meta_nprod(meta);
-    double lnKc = (npr - nre) * lnPf, fwd = 1.0, rev = 1.0;
-    for (int s = 0; s < nre; ++s) {
-      lnKc -= w.g[sl[s]];
-      fwd *= w.C[sl[s]];
-    }
-    for (int s = 0; s < npr; ++s) {
-      lnKc += w.g[sl[3 + s]];
-      rev *= w.C[sl[3 + s]];
-    }
-    double kr = kf * exp(-lnKc);
-    double q = kf * fwd - kr * rev;
-    int type = meta_type(meta);
-    if (type != 0) {
-      double M = Ctot;
-      int e0 = m.eff0[i], ne = meta_neff(meta);
-      for (int e = 0; e < ne; ++e) M += m.eff[e0 + e] * w.C[m.effsp[e0 + e]];
-      if (type == 1) {
-        q *= M;
-      } else {
-        TroeOut t = troe_factor<false>(m.troe + NTROE * meta_troe(meta), T, logT, invT, kf,
-                                       0.0, M);
-        q *= t.P;
-      }
-    }
-    for (int s = 0; s < nre; ++s) w.wd[sl[s]] -= q;
-    for (int s = 0; s < npr; ++s) w.wd[sl[3 + s]] += q;
-  }
-  double Hw = 0.0;
-  for (int k = 0; k < in; ++k) Hw += w.hs[k] * w.wd[k];
-  // f_T = -sum_k H_k wdot_k / (rho cp),  H_k = (h/RT) Ru T, cp = Ru cpm
-  f[0] = -(Hw * T) / (rho * cpm);
-  bool ok = isfinite(f[0]);
-  for (int k = 0; k < in; ++k) {
-    f[1 + k] = m.W[k] * w.wd[k] / rho;
-    ok &= isfinite(f[1 + k]);
-  }
-  return ok ? 0 : 4;
-}
-
-// ---------------------------------------------------------------------------
-// Analytical Jacobian J (row-major N x N, N = ns), assembled from the sparse
-// reaction structure:
-//   dq/dY_j = (rho/W_j) D_j - (rho/W_in) D_in - (m_j/S) sigma',
-//   D_k = dq/dC_k without the uniform [M] part (that part multiplies
-//   d(sum C)/dY_j = 0 at fixed T, P), m_j = 1/W_j - 1/W_in,
-//   dq/dT = dq/dT|_C - sigma/T with sigma = sum_k dq/dC_k C_k.
-// Rows: dY_k/dt = W_k wdot_k/rho and dT/dt = -sum H_k wdot_k/(rho cp) by
-// the product and quotient rules (rho, cp and H_k depend on y).
-// ---------------------------------------------------------------------------
-template <int MAXN>
-struct JacScratch {
-  double A[MAXN], B[MAXN], Tc[MAXN], dcp[MAXN], mj[MAXN];
-};
-
-template <int MAXN>
-__device__ __noinline__ int jac_analytic(const MechView &m, double P, const double *y, double *J,
-                            ChemScratch<MAXN> &w, JacScratch<MAXN> &x) {
-  const int ns = m.ns, in = ns - 1, N = ns;
-  const double T = y[0];
-  double sumY = 0.0, S = 0.0;
-  for (int k = 0; k < in; ++k) {
-    sumY += y[1 + k];
-    S += y[1 + k] * m.invW[k];
-  }
-  const double Yin = 1.0 - sumY;
-  S += Yin * m.invW[in];
-  const double rho = P / (RU * T * S);
-  const double logT = log(T), invT = 1.0 / T;
   double cpm = 0.0, dcpm = 0.0;
   for (int k = 0; k < ns; ++k) {
-    double Yk = (k < in) ? y[1 + k] : Yin;
+    const double Yk = (k < in) ? y[1 + k] : Yin;
     w.C[k] = rho * Yk * m.invW[k];
-    int r = range_of(m, k, T);
+    const int r = range_of(m, k, T);
     const double *cc = m.cp + (2 * k + r) * NCP;
-    double cp = poly_cp(cc, T);
-    double h = poly_h(m.h + (2 * k + r) * NH, T, invT);
-    double s = poly_s(m.s + (2 * k + r) * NS, T, logT);
+    const double cp = poly_cp(cc, T);
+    const double h = poly_h(m.h + (2 * k + r) * NH, T, invT);
+    const double s = poly_s(m.s + (2 * k + r) * NS, T, logT);
     w.g[k] = s - h;
     w.hs[k] = h;
     w.cpk[k] = cp;
-    x.dcp[k] = poly_dcp(cc, T);
     cpm += Yk * cp * m.invW[k];
-    dcpm += Yk * x.dcp[k] * m.invW[k];
     w.wd[k] = 0.0;
-    x.A[k] = 0.0;
-    x.B[k] = 0.0;
-    x.Tc[k] = 0.0;
+    if (wantJ) {
+      x.dcp[k] = poly_dcp(cc, T);
+      dcpm += Yk * x.dcp[k] * m.invW[k];
+      x.A[k] = JT(0);
+      x.B[k] = JT(0);
+      x.Tc[k] = JT(0);
+      x.Cj[k] = JT(w.C[k]);
+      x.rW[k] = JT(rho * m.invW[k]);
+    }
   }
-  for (int q = 0; q < N * N; ++q) J[q] = 0.0;
-  for (int j = 0; j < in; ++j) x.mj[j] = m.invW[j] - m.invW[in];
+  if (wantJ) {
+    for (int q = 0; q < N * N; ++q) J[q] = JT(0);
+    for (int j = 0; j < in; ++j) x.mj[j] = JT(m.invW[j] - m.invW[in]);
+  }
   const double Ctot = rho * S;
-  const double lnPf = log(PATM / RU) - logT;
+  const double lnPf = 2.5003366899611787 - logT;  // ln(Patm / Ru) - ln T
   for (int i = 0; i < m.nr; ++i) {
     const int meta = m.meta[i];
     const int *sl = m.slot + 6 * i;
     const int nre = meta_nreac(meta), npr = meta_nprod(meta), type = meta_type(meta);
-    double kf = exp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT);
-    double dlnkf = m.b[i] * invT + m.Th[i] * invT * invT;
+    const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
     double lnKc = (npr - nre) * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
     for (int s = 0; s < nre; ++s) {
       lnKc -= w.g[sl[s]];
@@ -307,11 +281,10 @@ __device__ __noinline__ int jac_analytic(const MechView &m, double P, const doub
       dH += w.hs[sl[3 + s]];
       rev *= w.C[sl[3 + s]];
     }
-    double kr = kf * exp(-lnKc);
-    // d ln Kc / dT = sum nu (h/RT) / T - (sum nu) / T
-    double dlnkr = dlnkf - (dH - (npr - nre)) * invT;
+    const double kr = kf * kexp(-lnKc, m.etab);
     double phi = 1.0, dphi_dT = 0.0, dphi_dM = 0.0, M = Ctot;
     const int e0 = m.eff0[i], ne = meta_neff(meta);
+    const double dlnkf = m.b[i] * invT + m.Th[i] * invT * invT;
     if (type != 0) {
       for (int e = 0; e < ne; ++e) M += m.eff[e0 + e] * w.C[m.effsp[e0 + e]];
       if (type == 1) {
@@ -327,87 +300,107 @@ __device__ __noinline__ int jac_analytic(const MechView &m, double P, const doub
     }
     const double Rn = kf * fwd - kr * rev;
     const double q = phi * Rn;
-    const double u = Rn * dphi_dM;
-    const double sig_p = phi * (nre * kf * fwd - npr * kr * rev) + u * (M - Ctot);
-    const double dqdT = phi * (kf * dlnkf * fwd - kr * dlnkr * rev) + Rn * dphi_dT -
-                        (sig_p + u * Ctot) * invT;
-    // row updates: nu = -1 per reactant slot, +1 per product slot
-    for (int rs = 0; rs < nre + npr; ++rs) {
-      const int row = (rs < nre) ? sl[rs] : sl[3 + rs - nre];
-      const double nu = (rs < nre) ? -1.0 : 1.0;
-      w.wd[row] += nu * q;
-      x.B[row] += nu * sig_p;
-      x.Tc[row] += nu * dqdT;
-      double *Jr = J + (1 + row) * N;
-      // mass-action columns
-      for (int cs = 0; cs < nre + npr; ++cs) {
-        const int col = (cs < nre) ? sl[cs] : sl[3 + cs - nre];
-        double p = 1.0;
-        if (cs < nre) {
-          for (int t = 0; t < nre; ++t)
-            if (t != cs) p *= w.C[sl[t]];
-          p *= phi * kf;
-        } else {
-          for (int t = 0; t < npr; ++t)
-            if (t != cs - nre) p *= w.C[sl[3 + t]];
-          p *= -phi * kr;
+    for (int s = 0; s < nre; ++s) w.wd[sl[s]] -= q;
+    for (int s = 0; s < npr; ++s) w.wd[sl[3 + s]] += q;
+    if (wantJ) {
+      // d ln Kc / dT = sum nu (h/RT) / T - (sum nu) / T
+      const double dlnkr = dlnkf - (dH - (npr - nre)) * invT;
+      const double u = Rn * dphi_dM;
+      const double sig_p = phi * (nre * kf * fwd - npr * kr * rev) + u * (M - Ctot);
+      const double dqdT = phi * (kf * dlnkf * fwd - kr * dlnkr * rev) + Rn * dphi_dT -
+                          (sig_p + u * Ctot) * invT;
+      const JT pkf = JT(phi * kf), pkr = JT(-phi * kr), uJ = JT(u);
+      const JT sJ = JT(sig_p), tJ = JT(dqdT);
+      for (int rs = 0; rs < nre + npr; ++rs) {
+        const int row = (rs < nre) ? sl[rs] : sl[3 + rs - nre];
+        const JT nu = (rs < nre) ? JT(-1) : JT(1);
+        x.B[row] += nu * sJ;
+        x.Tc[row] += nu * tJ;
+        JT *Jr = J + (1 + row) * N;
+        for (int cs = 0; cs < nre + npr; ++cs) {
+          const int col = (cs < nre) ? sl[cs] : sl[3 + cs - nre];
+          JT p = (cs < nre) ? pkf : pkr;
+          if (cs < nre) {
+            for (int t = 0; t < nre; ++t)
+              if (t != cs) p *= x.Cj[sl[t]];
+          } else {
+            for (int t = 0; t < npr; ++t)
+              if (t != cs - nre) p *= x.Cj[sl[3 + t]];
+          }
+          if (col != in)
+            Jr[1 + col] += nu * x.rW[col] * p;
+          else
+            x.A[row] += nu * p;
         }
-        if (col != in)
-          Jr[1 + col] += nu * rho * m.invW[col] * p;
-        else
-          x.A[row] += nu * p;
-      }
-      // efficiency columns
-      for (int e = 0; e < ne; ++e) {
-        const int col = m.effsp[e0 + e];
-        const double p = u * m.eff[e0 + e];
-        if (col != in)
-          Jr[1 + col] += nu * rho * m.invW[col] * p;
-        else
-          x.A[row] += nu * p;
+        for (int e = 0; e < ne; ++e) {
+          const int col = m.effsp[e0 + e];
+          const JT p = uJ * JT(m.eff[e0 + e]);
+          if (col != in)
+            Jr[1 + col] += nu * x.rW[col] * p;
+          else
+            x.A[row] += nu * p;
+        }
       }
     }
   }
-  // rank-one and inert terms, then the temperature column of dwdot/dy
-  const double rWin = rho * m.invW[in];
-  for (int k = 0; k < in; ++k) {
-    double *Jr = J + (1 + k) * N;
-    Jr[0] = x.Tc[k];
-    for (int j = 0; j < in; ++j) Jr[1 + j] -= rWin * x.A[k] + x.mj[j] / S * x.B[k];
-  }
-  // T row from the dwdot/dy rows (before they are scaled)
   double Hw = 0.0, CPw = 0.0;
   for (int k = 0; k < in; ++k) {
     Hw += w.hs[k] * w.wd[k];
     CPw += w.cpk[k] * w.wd[k];
   }
-  Hw *= RU * T;   // sum H_k wdot_k, J/(m^3 s)
-  CPw *= RU;      // sum Cp_k wdot_k
+  // f_T = -sum_k H_k wdot_k / (rho cp),  H_k = (h/RT) Ru T, cp = Ru cpm
+  f[0] = -(Hw * T) / (rho * cpm);
+  bool ok = isfinite(f[0]);
+  const double irho = 1.0 / rho;
+  for (int k = 0; k < in; ++k) {
+    f[1 + k] = m.W[k] * w.wd[k] * irho;
+    ok &= isfinite(f[1 + k]);
+  }
+  if (!wantJ) return ok ? 0 : 4;
+  // rank-one and inert terms, then the temperature column of dwdot/dy
+  const JT rWin = x.rW[in], iS = JT(1.0 / S);
+  for (int k = 0; k < in; ++k) {
+    JT *Jr = J + (1 + k) * N;
+    Jr[0] = x.Tc[k];
+    const JT a = rWin * x.A[k], b = iS * x.B[k];
+    for (int j = 0; j < in; ++j) Jr[1 + j] -= a + x.mj[j] * b;
+  }
+  // T row from the dwdot/dy rows (before they are scaled)
+  const double HwJ = Hw * RU * T;      // sum H_k wdot_k
+  const double CPwJ = CPw * RU;        // sum Cp_k wdot_k
   const double rcp = rho * cpm * RU;
   const double cpin = w.cpk[in] * m.invW[in];
+  const JT hfac = JT(RU * T / rcp);    // dHw/dy enters as -RU T sum h_k J_kc / rcp
+  const JT g2 = JT(HwJ / (rcp * rcp));
   for (int c = 0; c < N; ++c) {
-    double dHw = (c == 0) ? CPw : 0.0;
-    for (int k = 0; k < in; ++k) dHw += w.hs[k] * RU * T * J[(1 + k) * N + c];
-    double drho, dcp;
+    JT dh = JT(0);
+    for (int k = 0; k < in; ++k) dh += JT(w.hs[k]) * J[(1 + k) * N + c];
+    double drcp;
     if (c == 0) {
-      drho = -rho * invT;
-      dcp = dcpm * RU;
+      drcp = cpm * RU * (-rho * invT) + rho * dcpm * RU;
     } else {
-      drho = -rho * x.mj[c - 1] / S;
-      dcp = (w.cpk[c - 1] * m.invW[c - 1] - cpin) * RU;
+      drcp = cpm * RU * (-rho * (m.invW[c - 1] - m.invW[in]) / S) +
+             rho * (w.cpk[c - 1] * m.invW[c - 1] - cpin) * RU;
     }
-    const double drcp = cpm * RU * drho + rho * dcp;
-    J[c] = -dHw / rcp + Hw / (rcp * rcp) * drcp;
+    const JT extra = (c == 0) ? JT(-CPwJ / rcp) : JT(0);
+    J[c] = -hfac * dh + extra + g2 * JT(drcp);
   }
-  bool ok = true;
   for (int k = 0; k < in; ++k) {
-    double *Jr = J + (1 + k) * N;
-    const double a = m.W[k] / rho, bb = m.W[k] * w.wd[k] / (rho * rho);
-    Jr[0] = a * Jr[0] - bb * (-rho * invT);
-    for (int j = 0; j < in; ++j) Jr[1 + j] = a * Jr[1 + j] - bb * (-rho * x.mj[j] / S);
+    JT *Jr = J + (1 + k) * N;
+    const JT a = JT(m.W[k] * irho), bb = JT(m.W[k] * w.wd[k] * irho * irho);
+    Jr[0] = a * Jr[0] + bb * JT(rho * invT);
+    const JT bS = bb * JT(rho / S);
+    for (int j = 0; j < in; ++j) Jr[1 + j] = a * Jr[1 + j] + bS * x.mj[j];
   }
-  for (int q = 0; q < N * N; ++q) ok &= isfinite(J[q]);
+  for (int q = 0; q < N * N; ++q) ok &= isfinite(double(J[q]));
   return ok ? 0 : 4;
+}
+
+// f only (the Jacobian scratch is not touched when wantJ is false)
+template <int MAXN, typename JT>
+__device__ __forceinline__ int rhs(const MechView &m, double P, const double *y, double *f,
+                                   ChemScratch<MAXN> &w, JacScratch<MAXN, JT> &x) {
+  return chem_eval<MAXN, JT>(m, P, y, f, (JT *)nullptr, false, w, x);
 }
 
 // ---------------------------------------------------------------------------

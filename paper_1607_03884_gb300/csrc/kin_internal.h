@@ -1,0 +1,18 @@
+// Host-side helpers shared by the C-ABI translation units of libkin.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/kin.h"
+#include "kin_kernels.cuh"
+
+namespace kin {
+// Validate a mechanism description and build its device tables on the host.
+int build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double> &dt,
+                 std::vector<int> &it);
+// Upload the Radau constants to every kernel translation unit, once per device.
+int ensure_constants(int dev);
+// Launch the integration kernel that matches the options and species count.
+int launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms);
+}  // namespace kin

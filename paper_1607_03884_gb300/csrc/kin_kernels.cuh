@@ -88,31 +88,25 @@ __global__ void __launch_bounds__(64) k_integrate_queue(KernelArgs a) {
   unsigned long long *queue = a.totals + 9;
   Work<MAXN, LT> w;
   StepState s;
-  Machine<MAXN, LT, FDJ> mc;
   int64_t idx = -1;
   double P = 0.0;
-  // Each trip: (re)fill, one right-hand side, bookkeeping.  The trip count is
-  // bounded: every state takes at most max_steps steps of at most nit + 2 + N
-  // evaluations each, plus a constant; the guard stops a runaway lane.
-  for (long long trip = 0;; ++trip) {
+  // One step attempt per trip.  A lane whose state is finished stores it and
+  // pops the next index; every state ends after at most max_steps attempts
+  // (radau_step enforces it), so each lane's loop is bounded.
+  for (;;) {
     if (idx < 0) {
       const unsigned long long t = atomicAdd(queue, 1ull);
       if ((int64_t)t >= n) break;
       idx = (int64_t)t;
       P = a.P[idx];
       load_state(w, a, N, idx);
-      init_state<MAXN, LT>(s);
-      for (int k = 0; k < N; ++k) w.u[k] = w.y[k];
-      mc.phase = PH_F0_INIT;
-      trip = 0;
+      if (radau_init<MAXN, LT, FDJ>(m, P, w, s, a.rp, idx)) {
+        store_state(w, s, a, N, idx);
+        idx = -1;
+        continue;
+      }
     }
-    const int rc = rhs<MAXN>(m, P, w.u, w.fu, w.cs);
-    bool more = mc.advance(m, P, w, s, a.rp, idx, rc);
-    if (more && trip > (long long)a.rp.max_steps * (a.rp.nit * 3 + 4 + N) + 16) {
-      s.status = 1;
-      more = false;
-    }
-    if (!more) {
+    if (radau_step<MAXN, LT, FDJ>(m, P, w, s, a.rp, idx)) {
       store_state(w, s, a, N, idx);
       idx = -1;
     }

@@ -24,7 +24,7 @@ MAX_SPECIES = 64
 # every symbol include/kin.h declares
 EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integrate",
            "kin_integrate_ex", "kin_integrate_host", "kin_get_stats", "kin_rhs",
-           "kin_jacobian", "kin_radau_constants", "kin_status_string")
+           "kin_jacobian", "kin_radau_constants", "kin_status_string", "kin_exp")
 
 
 class KinError(RuntimeError):
@@ -75,6 +75,7 @@ def lib():
             L.kin_rhs.argtypes = [vp, vp, vp, i64, vp, vp]
             L.kin_jacobian.argtypes = [vp, vp, vp, i64, i32, d, vp, vp, vp]
             L.kin_radau_constants.argtypes = [vp, i32]
+            L.kin_exp.argtypes = [vp, vp, vp, i64, vp]
             L.kin_status_string.argtypes = [C.c_int]
             L.kin_status_string.restype = C.c_char_p
             _lib = L
@@ -117,6 +118,23 @@ def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7
     o.transform_tol = int(bool(transform_tol))
     o.h0, o.z0, o.h_first, o.z_first = _ptr(h0), _ptr(z0), _ptr(h_first), _ptr(z_first)
     return o
+
+
+def mech_desc(mech):
+    """(kin_mech_desc, arrays it points at) for a ``synth.Mechanism``-like object."""
+    arrs = dict(
+        W=np.ascontiguousarray(mech.W, np.float64),
+        nasa=np.ascontiguousarray(mech.nasa, np.float64),
+        reac=np.ascontiguousarray(mech.reac, np.int32),
+        prod=np.ascontiguousarray(mech.prod, np.int32),
+        arrh=np.ascontiguousarray(mech.arrh, np.float64),
+        rtype=np.ascontiguousarray(mech.rtype, np.int32),
+        eff=np.ascontiguousarray(mech.eff, np.float64),
+        fall=np.ascontiguousarray(mech.fall, np.float64))
+    d = MechDesc(int(mech.ns), int(mech.nr), *(arrs[k].ctypes.data for k in
+                                                ("W", "nasa", "reac", "prod", "arrh", "rtype",
+                                                 "eff", "fall")))
+    return d, arrs
 
 
 class Mechanism:
@@ -197,6 +215,10 @@ class Mechanism:
     def rhs(self, y, P, f, stream=None):
         n = int(P.shape[0])
         _check(lib().kin_rhs(self.handle, _ptr(y), _ptr(P), n, _ptr(f), _stream(stream)), "kin_rhs")
+
+    def exp(self, x, y, stream=None):
+        _check(lib().kin_exp(self.handle, _ptr(x), _ptr(y), int(x.numel()), _stream(stream)),
+               "kin_exp")
 
     def jacobian(self, y, P, J, fd=False, h=0.0, scal=None, stream=None):
         n = int(P.shape[0])
