@@ -183,6 +183,25 @@ int kin_rhs(kin_mech *m, const double *y, const double *P, int64_t n, double *f,
 int kin_jacobian(kin_mech *m, const double *y, const double *P, int64_t n, int32_t fd, double h,
                  const double *scal, double *J, void *stream);
 
+/* Size of the device array kin_integrate_static works in: 64 KiB for the
+ * mechanism tables plus 256 B of counters. */
+#define KIN_STATIC_SCRATCH_BYTES (64 * 1024 + 256)
+
+/* kin_integrate with the default options for callers that cannot allocate
+ * device memory (no cudaMalloc, cudaFree or allocating library call is made):
+ * the mechanism is passed as its host description and its tables, with the
+ * kernel's counters, go to a fixed device array inside libkin
+ * (KIN_STATIC_SCRATCH_BYTES) instead of a kin_mech's workspace.  The paper
+ * has no counterpart; it exists for hosts whose allocator owns the device
+ * memory.  Y, T, P and status are as for kin_integrate_ex (dev pointers).
+ * The first call on a device looks up the array's device address; make it
+ * before any stream capture.  Calls share the array: calls whose GPU work
+ * overlaps race and must not be issued.  Errors: as kin_integrate, plus
+ * KIN_ERR_UNSUPPORTED when the mechanism's tables exceed 64 KiB. */
+int kin_integrate_static(const kin_mech_desc *desc, double *Y, double *T, const double *P,
+                         int64_t n, double dt, double rtol, double atol, int32_t *status,
+                         void *stream);
+
 /* The exponential the rate kernels use (Tang's table-driven method, accurate
  * to about 1 ulp for |x| <= 700, the library exp beyond): y[i] = exp(x[i]) for
  * x, y dev [n].  Unit-level entry for testing; needs a mechanism only for

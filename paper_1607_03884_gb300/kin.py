@@ -24,7 +24,8 @@ MAX_SPECIES = 64
 # every symbol include/kin.h declares
 EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integrate",
            "kin_integrate_ex", "kin_integrate_host", "kin_get_stats", "kin_rhs",
-           "kin_jacobian", "kin_radau_constants", "kin_status_string", "kin_exp")
+           "kin_jacobian", "kin_radau_constants", "kin_status_string", "kin_exp",
+           "kin_integrate_static")
 
 
 class KinError(RuntimeError):
@@ -76,6 +77,7 @@ def lib():
             L.kin_jacobian.argtypes = [vp, vp, vp, i64, i32, d, vp, vp, vp]
             L.kin_radau_constants.argtypes = [vp, i32]
             L.kin_exp.argtypes = [vp, vp, vp, i64, vp]
+            L.kin_integrate_static.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp]
             L.kin_status_string.argtypes = [C.c_int]
             L.kin_status_string.restype = C.c_char_p
             _lib = L
@@ -135,6 +137,17 @@ def mech_desc(mech):
                                                 ("W", "nasa", "reac", "prod", "arrh", "rtype",
                                                  "eff", "fall")))
     return d, arrs
+
+
+def integrate_static(mech, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, status=None, stream=None):
+    """kin_integrate_static: default-option integration that allocates no device
+    memory (tables and counters in libkin's fixed device array)."""
+    d, keep = mech_desc(mech)
+    n = int(T.shape[0])
+    rc = lib().kin_integrate_static(C.byref(d), _ptr(Y), _ptr(T), _ptr(P), n, float(dt),
+                                    float(rtol), float(atol), _ptr(status), _stream(stream))
+    del keep
+    _check(rc, "kin_integrate_static")
 
 
 class Mechanism:
