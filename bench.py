@@ -39,7 +39,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dt", type=float, default=1e-4)
-    p.add_argument("--layout", default="queue", choices=["plain", "queue"])
+    p.add_argument("--layout", default="auto", choices=["auto", "plain", "queue"])
     p.add_argument("--fp32", type=int, default=1, help="FP32 Newton matrices (1) or FP64 (0)")
     p.add_argument("--n", type=int, default=0, help="states (0 = the workload's 2^20)")
     p.add_argument("--no-extras", action="store_true", help="skip the comparison legs")
@@ -154,8 +154,18 @@ def run_ours(args, rank, world):
     Y, T = Y0.clone(), T0.clone()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    opt = dict(layout=args.layout, lu_fp32=bool(args.fp32))
     ops = op_model(mech)
+    tune = None
+    if args.layout == "auto":
+        # autotuner (kin_autotune) on a 2^18-state prefix: layout, block, refill batch
+        m = min(n, 1 << 18)
+        best, secs = mg.autotune(Y0[:, :m].contiguous(), T0[:m].contiguous(), P[:m].contiguous(),
+                                 args.dt, RTOL, ATOL, stream=stream, lu_fp32=bool(args.fp32))
+        tune = {"states": m, "best": best, "candidate_seconds": [round(x, 4) for x in secs]}
+        opt = dict(layout=best["layout"], block=best["block"], queue_refill=best["queue_refill"],
+                   lu_fp32=bool(args.fp32))
+    else:
+        opt = dict(layout=args.layout, lu_fp32=bool(args.fp32))
 
     def barrier():
         if dist is not None:
@@ -193,13 +203,21 @@ def run_ours(args, rank, world):
     value = n * world / t_max
     f64, f32 = algorithmic_flops(tot, ops, bool(args.fp32))
 
-    out = {}
+    out = {"tune": tune, "opt": {k: v for k, v in opt.items()}}
     if rank == 0 and not args.no_extras:
+        Y_ours, T_ours = Y.cpu().numpy(), T.cpu().numpy()
         # the plain FP64 one-state-per-thread kernel on the same workload
         base_opt = dict(layout="plain", lu_fp32=False)
         one(args.dt, base_opt, False)
         tb = [one(args.dt, base_opt, True) for _ in range(max(1, min(args.steps, 2)))]
         out["plain_fp64_states_per_s"] = n / float(np.mean(tb))
+        # equal error: the paper's E_i (Sec. 2.3) of our result against the
+        # plain FP64 kernel's, at the requested tolerances
+        yo = np.concatenate([T_ours[None], Y_ours[:-1]])
+        yb = np.concatenate([T.cpu().numpy()[None], Y.cpu().numpy()[:-1]])
+        E = np.sqrt(np.mean(((yo - yb) / (ATOL + np.abs(yb) * RTOL)) ** 2, axis=0))
+        out["error_vs_plain_fp64"] = {"E_max": float(E.max()), "E_median": float(np.median(E)),
+                                      "E_p99": float(np.percentile(E, 99))}
         # dt = 1e-6 for both
         other = 1e-6 if args.dt != 1e-6 else 1e-4
         one(other, opt, False)
@@ -297,7 +315,7 @@ def main():
     a64 = r["f64"] / t / 1e12
     roof = {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": a64 / FP64_PEAK_TFLOPS, "traffic": None,
-            "pipe": "fp64", "kernel": f"k_integrate_{args.layout}",
+            "pipe": "fp64", "kernel": f"k_integrate_{r['extras']['opt'].get('layout')}",
             "peak_source": "152 SMs x 2 FP64 FMA/clk x 2.07 GHz (unit count measured)",
             "fp32_tflops": r["f32"] / t / 1e12}
     cb = cpu_baseline(args.cpu_sample, args.dt) if not args.no_extras else None
@@ -309,7 +327,9 @@ def main():
         "dtype": "f64+f32" if args.fp32 else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "states": r["n"], "species": r["mech"].ns,
                    "reactions": r["mech"].nr, "dt": args.dt, "rtol": RTOL, "atol": ATOL,
-                   "layout": args.layout, "newton_matrices": "fp32" if args.fp32 else "fp64",
+                   "layout": ex["opt"].get("layout"), "block": ex["opt"].get("block", 0),
+                   "queue_refill": ex["opt"].get("queue_refill", 0), "autotune": ex.get("tune"),
+                   "newton_matrices": "fp32" if args.fp32 else "fp64",
                    "l2": "flushed (256 MiB write) and inputs restored before each timed step"},
         "roofline": roof,
         "cpu_baseline": cb,
@@ -317,6 +337,9 @@ def main():
         "gpu_launches": args.steps,
         "clocks": r["clocks"],
         "plain_fp64_states_per_s": ex.get("plain_fp64_states_per_s"),
+        "vs_plain_fp64": (r["value"] / world / ex["plain_fp64_states_per_s"]
+                          if ex.get("plain_fp64_states_per_s") else None),
+        "error_vs_plain_fp64": ex.get("error_vs_plain_fp64"),
         "per_dt": ex.get("per_dt"),
         "counters": {k: int(v) for k, v in r["tot"].items()},
     }

@@ -96,7 +96,12 @@ enum {
                            loop trip is one step attempt per lane, and a lane
                            whose state is done takes the next one from an
                            atomic work queue (answers the warp divergence of
-                           Sec. 3.3: no lane waits for the slowest state) */
+                           Sec. 3.3: no lane waits for the slowest state) */,
+  KIN_LAYOUT_WARP = 2   /* one state per warp (ns <= 63): vectors over lanes,
+                           Newton matrices in shared memory, warp-cooperative
+                           LU and solves, rates in parallel over reactions;
+                           warps pop states from the atomic queue.  For large
+                           mechanisms (the per-block strategy of Sec. 3.3) */
 };
 
 /* Integration options.  kin_options_default fills the defaults. */
@@ -111,6 +116,10 @@ typedef struct {
   int32_t block;         /* threads per block; 0 = library choice          (0) */
   int32_t grid_per_sm;   /* QUEUE: resident blocks per SM; 0 = occupancy   (0) */
   int32_t transform_tol; /* 1: rtol' = 0.1 rtol^(2/3), atol' = rtol' atol/rtol (1) */
+  int32_t queue_refill;  /* QUEUE: a warp refills once at least this many of its
+                            lanes are idle (1..32), taking that many states
+                            with one atomic; 0 = 1                         (0) */
+  int32_t reserved;      /* must be 0                                      (0) */
   const double *h0;      /* dev [n] first internal step per state, or NULL  */
   const double *z0;      /* dev [3*ns][n] first-step stage guesses, or NULL */
   double *h_first;       /* dev [n] out: first accepted step, or NULL       */
@@ -165,6 +174,19 @@ int kin_integrate_host(kin_mech *m, double *Y, double *T, const double *P, int64
                        double rtol, double atol, const kin_options *opt, int32_t *status,
                        int32_t *counters, void *stream);
 
+/* Autotuner: time candidate launch configurations on the caller's states
+ * (Y, T, P dev, n states; copied, the inputs are not modified) and return the
+ * fastest in *best.  Candidates: PLAIN with 64 and 32 threads per block;
+ * QUEUE with 64 threads and refill batches 1, 4, 8, 16, 32 threads and
+ * refill 1 (so max_candidates <= 8).  The other option fields (precision,
+ * Jacobian, limits, h0/z0 must be NULL) come from base (NULL = defaults).
+ * seconds: host [max_candidates] or NULL, each candidate's device time in
+ * that order.  Allocates and frees temporary device copies of the states.
+ * Synchronises the stream. */
+int kin_autotune(kin_mech *m, const double *Y, const double *T, const double *P, int64_t n,
+                 double dt, double rtol, double atol, const kin_options *base, kin_options *best,
+                 double *seconds, int32_t max_candidates, void *stream);
+
 /* Totals of the last kin_integrate* call on this mechanism, reduced on the
  * device: out[0..6] = sums of the KIN_CNT_* counters 0..6, out[7] = number of
  * failed states, out[8] = largest per-state step count.  Synchronises the
@@ -215,6 +237,63 @@ int kin_exp(kin_mech *m, const double *x, double *y, int64_t n, void *stream);
  * (the estimate is (gamma/h I - J)^-1 (f0 + sum d_i z_i / h)).  len >= 27.
  * Needs no GPU. */
 int kin_radau_constants(double *out, int32_t len);
+
+/* ---------------------------------------------------------------------------
+ * Step/guess predictor (the learned part; the paper has no counterpart).
+ * An MLP x (din) -> 3 x [Linear(width) -> SiLU] -> Linear(dout) trained on
+ * first steps the integrator itself produced, predicting the first internal
+ * step (log h0) and the first step's Newton starting stages (3 N values),
+ * which kin_options.h0 / .z0 feed back to the integrator.  Radau keeps its
+ * error test and step control, so only rejected steps and Newton iterations
+ * can change.  precision 0: BF16 tensor-core GEMMs with FP32 accumulation,
+ * BF16 activations between layers, FP32 master weights and Adam; 1: FP32
+ * everywhere (a check mode).  Matrices are row-major [rows][features], FP32,
+ * device pointers unless stated.  Calls on one kin_mlp are stream-ordered
+ * (one stream at a time).
+ * ------------------------------------------------------------------------- */
+typedef struct kin_mlp kin_mlp;
+
+/* Create with seeded He-uniform weights and zero biases.  KIN_ERR_INVALID_ARG
+ * for sizes out of [1, 4096] (width >= 8) or an unknown precision. */
+int kin_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t precision, uint64_t seed,
+                   kin_mlp **out);
+void kin_mlp_destroy(kin_mlp *net);
+/* Parameter count of the layout W0 [din][width], b0, W1, b1, W2, b2,
+ * W3 [width][dout], b3 used by get/set (host arrays); -1 for NULL. */
+int64_t kin_mlp_num_params(const kin_mlp *net);
+int kin_mlp_get_params(kin_mlp *net, float *host, int64_t len);
+/* set also resets the optimiser state */
+int kin_mlp_set_params(kin_mlp *net, const float *host, int64_t len);
+/* Y [M][dout] = net(X [M][din]). */
+int kin_mlp_forward(kin_mlp *net, const float *X, float *Y, int64_t M, void *stream);
+/* Gradient of the mean squared error over X [M][din], targets T [M][dout]:
+ * grad_out dev [num_params] (same layout as get/set) or NULL, loss_out dev
+ * scalar or NULL.  Synchronises the stream when grad_out is given. */
+int kin_mlp_grad(kin_mlp *net, const float *X, const float *T, int64_t M, float *grad_out,
+                 float *loss_out, void *stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) on a minibatch. */
+int kin_mlp_train_step(kin_mlp *net, const float *X, const float *T, int64_t M, float lr,
+                       float *loss_out, void *stream);
+/* Column means and standard deviations (floored at 1e-12) of X [M][d]. */
+int kin_moments(const float *X, int64_t M, int32_t d, float *mean, float *stdv, void *stream);
+/* Network inputs for n states (Y dev [ns][n], T, P dev [n], all FP64):
+ * X [n][3 + ns] = [ln T, ln P, ln dt, log10(max(Y_k, 1e-12))], standardised
+ * with mean/stdv [3 + ns] unless both are NULL. */
+int kin_mlp_features(int32_t ns, const double *Y, const double *T, const double *P, int64_t n,
+                     double dt, const float *mean, const float *stdv, float *X, void *stream);
+/* Training targets [n][1 + nz] = [ln h, z_0..z_{nz-1}] from the integrator's
+ * first-step outputs h dev [n], z dev [nz][n] (kin_options.h_first /
+ * .z_first), standardised with mean/stdv [1 + nz] unless both are NULL. */
+int kin_mlp_targets(int32_t nz, const double *h, const double *z, int64_t n, const float *mean,
+                    const float *stdv, float *tgt, void *stream);
+/* Features -> network -> h0 dev [n] (exp of the de-standardised output 0,
+ * clipped to [1e-14, dt]) and z0 dev [3 ns][n] (outputs 1..3 ns) for
+ * kin_options.h0 / .z0; either output may be NULL.  The net must have
+ * din = 3 + ns and dout = 1 + 3 ns. */
+int kin_mlp_predict(kin_mlp *net, int32_t ns, const double *Y, const double *T, const double *P,
+                    int64_t n, double dt, const float *in_mean, const float *in_std,
+                    const float *out_mean, const float *out_std, double *h0, double *z0,
+                    void *stream);
 
 /* Message for a kin_status. */
 const char *kin_status_string(int status);

@@ -192,6 +192,8 @@ extern "C" int kin_options_default(kin_options *o) {
   o->block = 0;
   o->grid_per_sm = 0;
   o->transform_tol = 1;
+  o->queue_refill = 0;
+  o->reserved = 0;
   return KIN_OK;
 }
 
@@ -283,6 +285,18 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
   L.ieff0 = q; q += nr;
   L.itroe = q;
   L.ieffsp = q; q += (neff > 0 ? neff : 1);
+  // species-major list of (reaction, net coefficient) for gathered production rates
+  std::vector<std::vector<int>> sp_list(ns);
+  for (int i = 0; i < nr; ++i)
+    for (int k = 0; k < ns; ++k) {
+      int nu = 0;
+      for (int s2 = 0; s2 < 3; ++s2) nu += (d->prod[3 * i + s2] == k) - (d->reac[3 * i + s2] == k);
+      if (nu != 0) sp_list[k].push_back((i << 4) | (nu + 8));
+    }
+  int ncsr = 0;
+  for (int k = 0; k < ns; ++k) ncsr += (int)sp_list[k].size();
+  L.icsr0 = q; q += ns + 1;
+  L.icsr = q; q += (ncsr > 0 ? ncsr : 1);
   L.ni = q;
   dt.assign(L.nd, 0.0);
   it.assign(L.ni, 0);
@@ -345,6 +359,14 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
     }
     it[L.imeta + i] = t | (nre << 2) | (npr << 4) | (ne << 8) | (troe_idx << 16);
   }
+  {
+    int c = 0;
+    for (int k = 0; k < ns; ++k) {
+      it[L.icsr0 + k] = c;
+      for (int code : sp_list[k]) it[L.icsr + c++] = code;
+    }
+    it[L.icsr0 + ns] = c;
+  }
   if (smem_bytes(L) > 200 * 1024) return KIN_ERR_UNSUPPORTED;
   return KIN_OK;
 }
@@ -399,7 +421,8 @@ extern "C" void kin_destroy(kin_mech *m) {
 
 int kin::launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t st,
                          int sms) {
-  if (a.L.ns <= 16) return o.lu_fp32 ? kin_launch_16f(a, o, st, sms) : kin_launch_16d(a, o, st, sms);
+  if (a.L.ns <= 16 && o.layout != KIN_LAYOUT_WARP)
+    return o.lu_fp32 ? kin_launch_16f(a, o, st, sms) : kin_launch_16d(a, o, st, sms);
   return o.lu_fp32 ? kin_launch_64f(a, o, st, sms) : kin_launch_64d(a, o, st, sms);
 }
 
@@ -423,8 +446,10 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   } else {
     kin_options_default(&o);
   }
-  if (o.layout != KIN_LAYOUT_PLAIN && o.layout != KIN_LAYOUT_QUEUE) return KIN_ERR_INVALID_ARG;
+  if (o.layout != KIN_LAYOUT_PLAIN && o.layout != KIN_LAYOUT_QUEUE && o.layout != KIN_LAYOUT_WARP)
+    return KIN_ERR_INVALID_ARG;
   if (o.nit < 1 || o.nit > 50 || o.max_steps < 1) return KIN_ERR_INVALID_ARG;
+  if (o.queue_refill < 0 || o.queue_refill > 32 || o.reserved != 0) return KIN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   m->last_stream = st;
   KIN_CUDA_TRY(cudaMemsetAsync(m->d_totals, 0, sizeof(unsigned long long) * 16, st));
@@ -456,6 +481,7 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   a.rp.z0 = o.z0;
   a.rp.h_first = o.h_first;
   a.rp.z_first = o.z_first;
+  a.refill_min = o.queue_refill > 0 ? o.queue_refill : 1;
   int dev = 0, sms = 0;
   KIN_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != m->device) return KIN_ERR_INVALID_ARG;
@@ -565,5 +591,86 @@ extern "C" int kin_exp(kin_mech *m, const double *x, double *y, int64_t n, void 
   k_exp<<<(unsigned)((n + block - 1) / block), block, 0, (cudaStream_t)stream>>>(
       m->d_tab + m->L.dexp, x, y, n);
   KIN_CUDA_TRY(cudaGetLastError());
+  return KIN_OK;
+}
+
+extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const double *P,
+                            int64_t n, double dt, double rtol, double atol, const kin_options *base,
+                            kin_options *best, double *seconds, int32_t max_candidates,
+                            void *stream) {
+  int rc = check_common(m, Y, T, P, n, dt, rtol, atol);
+  if (rc) return rc;
+  if (!best || n < 1 || max_candidates < 1) return KIN_ERR_INVALID_ARG;
+  kin_options b;
+  if (base) {
+    b = *base;
+  } else {
+    kin_options_default(&b);
+  }
+  if (b.h0 || b.z0 || b.h_first || b.z_first) return KIN_ERR_INVALID_ARG;
+  struct Cand {
+    int layout, block, refill;
+  };
+  const Cand cands[] = {{KIN_LAYOUT_PLAIN, 64, 0}, {KIN_LAYOUT_PLAIN, 32, 0},
+                        {KIN_LAYOUT_QUEUE, 64, 1}, {KIN_LAYOUT_QUEUE, 64, 4},
+                        {KIN_LAYOUT_QUEUE, 64, 8}, {KIN_LAYOUT_QUEUE, 64, 16},
+                        {KIN_LAYOUT_QUEUE, 64, 32}, {KIN_LAYOUT_QUEUE, 32, 1}};
+  const int nc = (int)(sizeof cands / sizeof cands[0]) < max_candidates
+                     ? (int)(sizeof cands / sizeof cands[0])
+                     : max_candidates;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ns = m->L.ns;
+  double *y = nullptr, *t = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best_i = -1;
+  float best_ms = 0.0f;
+  auto cleanup = [&]() {
+    cudaFree(y);
+    cudaFree(t);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&y, sizeof(double) * n * ns) != cudaSuccess ||
+      cudaMalloc(&t, sizeof(double) * n) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cleanup();
+    return KIN_ERR_NOMEM;
+  }
+  // the first candidate runs twice: the first launch also pays one-time costs
+  for (int run = -1; run < nc; ++run) {
+    const Cand &c = cands[run < 0 ? 0 : run];
+    kin_options o = b;
+    o.layout = c.layout;
+    o.block = c.block;
+    o.queue_refill = c.refill;
+    if (cudaMemcpyAsync(y, Y, sizeof(double) * n * ns, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(t, T, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaEventRecord(e0, st) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cleanup();
+      return KIN_ERR_CUDA;
+    }
+    rc = kin_integrate_ex(m, y, t, P, n, dt, rtol, atol, &o, nullptr, nullptr, stream);
+    float ms = 0.0f;
+    if (rc || cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cleanup();
+      return rc ? rc : KIN_ERR_CUDA;
+    }
+    if (run < 0) continue;
+    if (seconds) seconds[run] = ms * 1e-3;
+    if (best_i < 0 || ms < best_ms) {
+      best_i = run;
+      best_ms = ms;
+    }
+  }
+  cleanup();
+  *best = b;
+  best->layout = cands[best_i].layout;
+  best->block = cands[best_i].block;
+  best->queue_refill = cands[best_i].refill;
   return KIN_OK;
 }

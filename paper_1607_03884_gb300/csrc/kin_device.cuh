@@ -32,6 +32,7 @@ struct MechLayout {
   int dW, dinvW, dTmid, dcp, dh, ds, dlnA, db, dTh, dtroe, deff, dexp;
   // int-table offsets
   int islot, imeta, ieff0, itroe, ieffsp;
+  int icsr0, icsr;  // species -> (reaction, net nu) lists: offsets [ns+1], entries
 };
 
 // per-species coefficient blocks (two ranges each):
@@ -54,6 +55,7 @@ struct MechView {
   int ns, nr;
   const double *W, *invW, *Tmid, *cp, *h, *s, *lnA, *b, *Th, *troe, *eff, *etab;
   const int *slot, *meta, *eff0, *effsp;
+  const int *csr0, *csr;  // entry = reaction << 4 | (nu + 8)
 };
 
 __device__ __forceinline__ MechView make_view(const MechLayout &L, const double *d, const int *i) {
@@ -76,6 +78,8 @@ __device__ __forceinline__ MechView make_view(const MechLayout &L, const double 
   v.meta = i + L.imeta;
   v.eff0 = i + L.ieff0;
   v.effsp = i + L.ieffsp;
+  v.csr0 = i + L.icsr0;
+  v.csr = i + L.icsr;
   return v;
 }
 

@@ -6,6 +6,7 @@
 
 #include "../../include/kin.h"
 #include "kin_radau.cuh"
+#include "kin_warp.cuh"
 
 namespace kin {
 
@@ -18,7 +19,7 @@ namespace kin {
     }                                                                         \
   } while (0)
 
-inline size_t smem_bytes(const MechLayout &L) {
+__host__ __device__ inline size_t smem_bytes(const MechLayout &L) {
   return sizeof(double) * (size_t)L.nd + sizeof(int) * (size_t)L.ni;
 }
 
@@ -31,6 +32,7 @@ struct KernelArgs {
   int32_t *status, *counters;
   unsigned long long *totals;
   RadauParams rp;
+  int refill_min;  // QUEUE: idle lanes of a warp that trigger a refill
 };
 
 template <int MAXN, typename LT>
@@ -85,36 +87,140 @@ __global__ void __launch_bounds__(64) k_integrate_queue(KernelArgs a) {
   const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
   const int N = m.ns;
   const int64_t n = a.rp.n;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   unsigned long long *queue = a.totals + 9;
   Work<MAXN, LT> w;
   StepState s;
   int64_t idx = -1;
   double P = 0.0;
-  // One step attempt per trip.  A lane whose state is finished stores it and
-  // pops the next index; every state ends after at most max_steps attempts
-  // (radau_step enforces it), so each lane's loop is bounded.
+  bool exhausted = false;  // warp-uniform: the queue has no more states
+  // One step attempt per trip for every lane that holds a state.  Idle lanes
+  // wait until refill_min of the warp's lanes are idle, then take that many
+  // states with one atomic, so refilled lanes start their integrations
+  // together.  Every state ends after at most max_steps attempts, so the
+  // warp's loop is bounded.
   for (;;) {
-    if (idx < 0) {
-      const unsigned long long t = atomicAdd(queue, 1ull);
-      if ((int64_t)t >= n) break;
-      idx = (int64_t)t;
-      P = a.P[idx];
-      load_state(w, a, N, idx);
-      if (radau_init<MAXN, LT, FDJ>(m, P, w, s, a.rp, idx)) {
-        store_state(w, s, a, N, idx);
-        idx = -1;
-        continue;
+    const unsigned idle = __ballot_sync(FULL, idx < 0);
+    if (exhausted && idle == FULL) break;
+    const int nidle = __popc(idle);
+    if (!exhausted && nidle >= a.refill_min) {
+      const int leader = __ffs(idle) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(queue, (unsigned long long)nidle);
+      base = __shfl_sync(FULL, base, leader);
+      if (base + (unsigned long long)nidle >= (unsigned long long)n) exhausted = true;
+      if (idx < 0) {
+        const unsigned long long t = base + __popc(idle & ((1u << lane) - 1u));
+        if (t < (unsigned long long)n) {
+          idx = (int64_t)t;
+          P = a.P[idx];
+          load_state(w, a, N, idx);
+          if (radau_init<MAXN, LT, FDJ>(m, P, w, s, a.rp, idx)) {
+            store_state(w, s, a, N, idx);
+            idx = -1;
+          }
+        }
       }
     }
-    if (radau_step<MAXN, LT, FDJ>(m, P, w, s, a.rp, idx)) {
+    if (idx >= 0 && radau_step<MAXN, LT, FDJ>(m, P, w, s, a.rp, idx)) {
       store_state(w, s, a, N, idx);
       idx = -1;
     }
   }
 }
 
+// WARP layout: one state per warp, warps pop states from the atomic queue.
+template <typename LT, bool FDJ>
+__global__ void __launch_bounds__(128) k_integrate_warp(KernelArgs a) {
+  extern __shared__ double smem[];
+  const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
+  const int N = m.ns, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = a.rp.n;
+  char *base = reinterpret_cast<char *>(smem) + (smem_bytes(a.L) + 15) / 16 * 16 +
+               (size_t)warp * warp_buf_bytes(N, m.nr, sizeof(LT));
+  const WarpBuf<LT> b = carve_warp_buf<LT>(base, N, m.nr);
+  unsigned long long *queue = a.totals + 9;
+  WState w;
+  StepState s;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1ull);
+    t = __shfl_sync(WFULL, t, 0);
+    if (t >= (unsigned long long)n) break;
+    const int64_t idx = (int64_t)t;
+    const double P = a.P[idx];
+#pragma unroll
+    for (int r = 0; r < WR; ++r) {
+      const int g = lane + 32 * r;
+      w.y.v[r] = (g == 0) ? a.T[idx] : (g < N ? a.Y[(int64_t)(g - 1) * n + idx] : 0.0);
+    }
+    // every attempt ends the loop or counts a step; max_steps bounds it
+    bool done = warp_init<LT, FDJ>(m, b, P, w, s, a.rp, idx);
+    while (!done) done = warp_step<LT, FDJ>(m, b, P, w, s, a.rp, idx);
+    double sum = 0.0;
+#pragma unroll
+    for (int r = 0; r < WR; ++r) {
+      const int g = lane + 32 * r;
+      if (g == 0) a.T[idx] = w.y.v[r];
+      if (g >= 1 && g < N) {
+        a.Y[(int64_t)(g - 1) * n + idx] = w.y.v[r];
+        sum += w.y.v[r];
+      }
+    }
+    sum = wsum(sum);
+    if (lane == 0) {
+      a.Y[(int64_t)(N - 1) * n + idx] = 1.0 - sum;
+      if (a.status) a.status[idx] = s.status;
+      if (a.counters) {
+        const int32_t c[8] = {s.nstep, s.naccpt, s.nrejct, s.nfcn, s.njac, s.ndec, s.nsol,
+                              s.status};
+        for (int q = 0; q < 8; ++q) a.counters[(int64_t)q * n + idx] = c[q];
+      }
+      const unsigned long long c7[7] = {
+          (unsigned long long)s.nstep, (unsigned long long)s.naccpt, (unsigned long long)s.nrejct,
+          (unsigned long long)s.nfcn,  (unsigned long long)s.njac,   (unsigned long long)s.ndec,
+          (unsigned long long)s.nsol};
+      for (int q = 0; q < 7; ++q) atomicAdd(a.totals + q, c7[q]);
+      if (s.status) atomicAdd(a.totals + 7, 1ull);
+      atomicMax(a.totals + 8, (unsigned long long)s.nstep);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename LT, bool FDJ>
+int launch_warp(const KernelArgs &a, cudaStream_t st, int sms) {
+  const size_t tab = (smem_bytes(a.L) + 15) / 16 * 16;
+  const size_t wb = warp_buf_bytes(a.L.ns, a.L.nr, sizeof(LT));
+  const size_t budget = 227 * 1024;
+  if (tab + wb > budget) return KIN_ERR_UNSUPPORTED;
+  int warps = (int)((budget - tab) / wb);
+  if (warps > 4) warps = 4;
+  const size_t sm = tab + (size_t)warps * wb;
+  auto kern = k_integrate_warp<LT, FDJ>;
+  KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int per_sm = 0;
+  KIN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, sm));
+  if (per_sm < 1) return KIN_ERR_UNSUPPORTED;
+  int64_t grid = (int64_t)sms * per_sm;
+  const int64_t need = (a.rp.n + warps - 1) / warps;
+  if (grid > need) grid = need;
+  kern<<<(unsigned)grid, 32 * warps, sm, st>>>(a);
+  KIN_CUDA_TRY(cudaGetLastError());
+  return KIN_OK;
+}
+
 template <int MAXN, typename LT, bool FDJ>
 int launch_t(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms) {
+  if (o.layout == KIN_LAYOUT_WARP) {
+    if constexpr (MAXN == 64) {
+      if (a.L.ns > 63) return KIN_ERR_UNSUPPORTED;
+      return launch_warp<LT, FDJ>(a, st, sms);
+    } else {
+      return KIN_ERR_UNSUPPORTED;
+    }
+  }
   const size_t sm = smem_bytes(a.L);
   const int block = o.block > 0 ? o.block : 64;
   if (block > 64 || block % 32) return KIN_ERR_INVALID_ARG;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libkin.so")
 
 KIN_OK, KIN_ERR_INVALID_ARG, KIN_ERR_CUDA, KIN_ERR_NOMEM, KIN_ERR_MECH = 0, 1, 2, 3, 4
 KIN_ERR_STATE_FAILED, KIN_ERR_UNSUPPORTED = 5, 6
-LAYOUT_PLAIN, LAYOUT_QUEUE = 0, 1
+LAYOUT_PLAIN, LAYOUT_QUEUE, LAYOUT_WARP = 0, 1, 2
 COUNTER_NAMES = ("nstep", "naccpt", "nrejct", "nfcn", "njac", "ndec", "nsol", "status")
 MAX_SPECIES = 64
 
@@ -25,7 +25,10 @@ MAX_SPECIES = 64
 EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integrate",
            "kin_integrate_ex", "kin_integrate_host", "kin_get_stats", "kin_rhs",
            "kin_jacobian", "kin_radau_constants", "kin_status_string", "kin_exp",
-           "kin_integrate_static")
+           "kin_integrate_static", "kin_mlp_create", "kin_mlp_destroy", "kin_mlp_num_params",
+           "kin_mlp_get_params", "kin_mlp_set_params", "kin_mlp_forward", "kin_mlp_grad",
+           "kin_mlp_train_step", "kin_moments", "kin_mlp_features", "kin_mlp_targets",
+           "kin_mlp_predict", "kin_autotune")
 
 
 class KinError(RuntimeError):
@@ -45,7 +48,7 @@ class Options(C.Structure):
     _fields_ = [("layout", C.c_int32), ("lu_fp32", C.c_int32), ("jac_fd", C.c_int32),
                 ("max_steps", C.c_int32), ("nit", C.c_int32), ("block", C.c_int32),
                 ("grid_per_sm", C.c_int32), ("transform_tol", C.c_int32),
-                ("h0", C.c_void_p), ("z0", C.c_void_p), ("h_first", C.c_void_p),
+                ("queue_refill", C.c_int32), ("reserved", C.c_int32), ("h0", C.c_void_p), ("z0", C.c_void_p), ("h_first", C.c_void_p),
                 ("z_first", C.c_void_p)]
 
 
@@ -78,6 +81,22 @@ def lib():
             L.kin_radau_constants.argtypes = [vp, i32]
             L.kin_exp.argtypes = [vp, vp, vp, i64, vp]
             L.kin_integrate_static.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp]
+            L.kin_autotune.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp, vp, i32, vp]
+            L.kin_mlp_create.argtypes = [i32, i32, i32, i32, C.c_uint64, C.POINTER(vp)]
+            L.kin_mlp_destroy.argtypes = [vp]
+            L.kin_mlp_destroy.restype = None
+            L.kin_mlp_num_params.argtypes = [vp]
+            L.kin_mlp_num_params.restype = i64
+            L.kin_mlp_get_params.argtypes = [vp, vp, i64]
+            L.kin_mlp_set_params.argtypes = [vp, vp, i64]
+            L.kin_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
+            L.kin_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+            L.kin_mlp_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
+            L.kin_moments.argtypes = [vp, i64, i32, vp, vp, vp]
+            L.kin_mlp_features.argtypes = [i32, vp, vp, vp, i64, d, vp, vp, vp, vp]
+            L.kin_mlp_targets.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp]
+            L.kin_mlp_predict.argtypes = [vp, i32, vp, vp, vp, i64, d, vp, vp, vp, vp, vp, vp,
+                                          vp]
             L.kin_status_string.argtypes = [C.c_int]
             L.kin_status_string.restype = C.c_char_p
             _lib = L
@@ -106,10 +125,12 @@ def _stream(stream):
 
 
 def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7, block=0,
-            grid_per_sm=0, transform_tol=True, h0=None, z0=None, h_first=None, z_first=None):
+            grid_per_sm=0, transform_tol=True, queue_refill=0, h0=None, z0=None, h_first=None,
+            z_first=None):
     o = Options()
     _check(lib().kin_options_default(C.byref(o)), "kin_options_default")
-    o.layout = {"plain": LAYOUT_PLAIN, "queue": LAYOUT_QUEUE}[layout] if isinstance(layout, str) \
+    o.layout = {"plain": LAYOUT_PLAIN, "queue": LAYOUT_QUEUE, "warp": LAYOUT_WARP}[layout] \
+        if isinstance(layout, str) \
         else int(layout)
     o.lu_fp32 = int(bool(lu_fp32))
     o.jac_fd = int(bool(jac_fd))
@@ -118,6 +139,7 @@ def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7
     o.block = int(block)
     o.grid_per_sm = int(grid_per_sm)
     o.transform_tol = int(bool(transform_tol))
+    o.queue_refill = int(queue_refill)
     o.h0, o.z0, o.h_first, o.z_first = _ptr(h0), _ptr(z0), _ptr(h_first), _ptr(z_first)
     return o
 
@@ -215,6 +237,19 @@ class Mechanism:
                                       _ptr(counters), _stream(stream) if stream is not None else None)
         _check(rc, "kin_integrate_host")
 
+    def autotune(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, stream=None, **base):
+        """kin_autotune: returns (best options as a dict, list of candidate seconds)."""
+        b = options(**base)
+        best = Options()
+        secs = np.zeros(8)
+        rc = lib().kin_autotune(self.handle, _ptr(Y), _ptr(T), _ptr(P), int(T.shape[0]), float(dt),
+                                float(rtol), float(atol), C.byref(b), C.byref(best),
+                                secs.ctypes.data, 8, _stream(stream))
+        _check(rc, "kin_autotune")
+        layout = {LAYOUT_PLAIN: "plain", LAYOUT_QUEUE: "queue", LAYOUT_WARP: "warp"}[best.layout]
+        return dict(layout=layout, block=best.block, queue_refill=best.queue_refill,
+                    grid_per_sm=best.grid_per_sm), secs.tolist()
+
     def stats(self):
         """Totals of the last integration (kin_get_stats)."""
         out = np.zeros(9, dtype=np.int64)
@@ -245,3 +280,73 @@ def radau_constants():
     _check(lib().kin_radau_constants(out.ctypes.data, 27), "kin_radau_constants")
     return dict(c=out[0:3], gamma=out[3], alpha=out[4], beta=out[5],
                 T=out[6:15].reshape(3, 3), TI=out[15:24].reshape(3, 3), d=out[24:27])
+
+
+class MLP:
+    """The step/guess predictor (kin_mlp_*).  precision: "bf16" or "fp32"."""
+
+    def __init__(self, din, width, dout, precision="bf16", seed=0):
+        h = C.c_void_p()
+        p = {"bf16": 0, "fp32": 1}[precision]
+        _check(lib().kin_mlp_create(int(din), int(width), int(dout), p, int(seed), C.byref(h)),
+               "kin_mlp_create")
+        self._h = h
+        self.din, self.width, self.dout = int(din), int(width), int(dout)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.kin_mlp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        return int(lib().kin_mlp_num_params(self._h))
+
+    def get_params(self):
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        _check(lib().kin_mlp_get_params(self._h, out.ctypes.data, out.size), "kin_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().kin_mlp_set_params(self._h, p.ctypes.data, p.size), "kin_mlp_set_params")
+
+    def forward(self, X, Y, stream=None):
+        _check(lib().kin_mlp_forward(self._h, _ptr(X), _ptr(Y), int(X.shape[0]), _stream(stream)),
+               "kin_mlp_forward")
+
+    def grad(self, X, T, grad_out=None, loss_out=None, stream=None):
+        _check(lib().kin_mlp_grad(self._h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grad_out),
+                                  _ptr(loss_out), _stream(stream)), "kin_mlp_grad")
+
+    def train_step(self, X, T, lr, loss_out=None, stream=None):
+        _check(lib().kin_mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),
+                                        _ptr(loss_out), _stream(stream)), "kin_mlp_train_step")
+
+    def predict(self, ns, Y, T, P, dt, norm, h0=None, z0=None, stream=None):
+        """norm: dict of device float tensors in_mean, in_std, out_mean, out_std."""
+        _check(lib().kin_mlp_predict(self._h, int(ns), _ptr(Y), _ptr(T), _ptr(P), int(T.shape[0]),
+                                     float(dt), _ptr(norm["in_mean"]), _ptr(norm["in_std"]),
+                                     _ptr(norm["out_mean"]), _ptr(norm["out_std"]), _ptr(h0),
+                                     _ptr(z0), _stream(stream)), "kin_mlp_predict")
+
+
+def moments(X, mean, std, stream=None):
+    _check(lib().kin_moments(_ptr(X), int(X.shape[0]), int(X.shape[1]), _ptr(mean), _ptr(std),
+                             _stream(stream)), "kin_moments")
+
+
+def features(ns, Y, T, P, dt, X, mean=None, std=None, stream=None):
+    _check(lib().kin_mlp_features(int(ns), _ptr(Y), _ptr(T), _ptr(P), int(T.shape[0]), float(dt),
+                                  _ptr(mean), _ptr(std), _ptr(X), _stream(stream)),
+           "kin_mlp_features")
+
+
+def targets(nz, h, z, tgt, mean=None, std=None, stream=None):
+    _check(lib().kin_mlp_targets(int(nz), _ptr(h), _ptr(z), int(h.shape[0]), _ptr(mean),
+                                 _ptr(std), _ptr(tgt), _stream(stream)), "kin_mlp_targets")

@@ -1,0 +1,120 @@
+"""The step/guess predictor's CUDA kernels against the FP64 numpy reference
+(oracle/mlp.py): forward values, loss gradients (BF16 tensor-core mode to
+~2 %, FP32 check mode to 1e-5), Adam training progress, and the feature /
+target / prediction kernels that connect it to the integrator."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp as M  # noqa: E402
+from paper_1607_03884_gb300 import kin, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kin.lib()
+
+
+def unpack(p, din, w, dout):
+    sizes = [din, w, w, w, dout]
+    W, b, q = [], [], 0
+    for a, c in zip(sizes[:-1], sizes[1:]):
+        W.append(p[q:q + a * c].reshape(a, c).astype(np.float64))
+        q += a * c
+        b.append(p[q:q + c].astype(np.float64))
+        q += c
+    assert q == p.size
+    return W, b
+
+
+def bf16(x):
+    return torch.from_numpy(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 3e-2)])
+@pytest.mark.parametrize("din,w,dout,n", [(16, 64, 40, 77), (56, 32, 160, 130)])
+def test_forward_and_gradients_against_fp64_reference(precision, tol, din, w, dout, n):
+    rng = np.random.default_rng(din + w)
+    net = kin.MLP(din, w, dout, precision=precision, seed=3)
+    p = net.get_params()
+    p[:] += rng.normal(0, 0.01, p.size).astype(np.float32)   # nonzero biases too
+    net.set_params(p)
+    X = rng.normal(size=(n, din)).astype(np.float32)
+    T = rng.normal(size=(n, dout)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    Y = torch.empty((n, dout), dtype=torch.float32, device="cuda")
+    net.forward(Xd, Y)
+    g = torch.empty(net.num_params(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.grad(Xd, Td, grad_out=g, loss_out=loss)
+    W, b = unpack(p.astype(np.float64), din, w, dout)
+    x = X.astype(np.float64)
+    if precision == "bf16":
+        W = [bf16(Wl) for Wl in W]
+        x = bf16(x)
+    y, cache = M.forward(W, b, x)
+    gW, gb = M.backward(W, b, cache, y, T.astype(np.float64))
+    ref = np.concatenate([np.concatenate([a.ravel(), c]) for a, c in zip(gW, gb)])
+    yg = Y.cpu().numpy()
+    assert np.linalg.norm(yg - y) / np.linalg.norm(y) < tol
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - ref) / np.linalg.norm(ref) < tol
+    assert abs(loss.item() - M.loss(y, T)) / M.loss(y, T) < tol
+
+
+def test_training_reduces_loss_on_device():
+    rng = np.random.default_rng(0)
+    n, din, dout = 4096, 16, 40
+    X = rng.normal(size=(n, din)).astype(np.float32)
+    Wt = rng.normal(size=(din, dout)) / 4
+    T = np.tanh(X @ Wt).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    net = kin.MLP(din, 64, dout, precision="bf16", seed=1)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    losses = []
+    for it in range(300):
+        i = (it * 512) % n
+        net.train_step(Xd[i:i + 512], Td[i:i + 512], 2e-3, loss_out=loss)
+        losses.append(loss.item())
+    assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:5]), (losses[:5], losses[-5:])
+
+
+def test_feature_target_and_prediction_kernels():
+    mech = synth.make_mechanism("h2")
+    st = synth.make_states(mech, 300, seed=4)
+    ns, n = mech.ns, st.n
+    Y, T, P = (torch.from_numpy(a).cuda() for a in (st.Y, st.T, st.P))
+    X = torch.empty((n, 3 + ns), dtype=torch.float32, device="cuda")
+    kin.features(ns, Y, T, P, 1e-4, X)
+    want = np.concatenate([np.log(st.T)[:, None], np.log(st.P)[:, None],
+                           np.full((n, 1), np.log(1e-4)),
+                           np.log10(np.maximum(st.Y.T, 1e-12))], axis=1)
+    np.testing.assert_allclose(X.cpu().numpy(), want, rtol=2e-6, atol=2e-6)
+    mean = torch.empty(3 + ns, dtype=torch.float32, device="cuda")
+    std = torch.empty_like(mean)
+    kin.moments(X, mean, std)
+    np.testing.assert_allclose(mean.cpu().numpy(), want.mean(0), rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(std.cpu().numpy(), np.maximum(want.std(0), 1e-12), rtol=1e-4, atol=1e-6)
+    h = torch.from_numpy(np.linspace(1e-9, 1e-6, n)).cuda()
+    z = torch.from_numpy(np.arange(3 * ns * n, dtype=np.float64).reshape(3 * ns, n)).cuda()
+    tg = torch.empty((n, 1 + 3 * ns), dtype=torch.float32, device="cuda")
+    kin.targets(3 * ns, h, z, tg)
+    tgn = tg.cpu().numpy()
+    np.testing.assert_allclose(tgn[:, 0], np.log(h.cpu().numpy()), rtol=1e-6)
+    np.testing.assert_allclose(tgn[:, 1:], z.cpu().numpy().T, rtol=1e-6)
+    # prediction: an untrained net gives finite, clipped h0 and finite z0
+    net = kin.MLP(3 + ns, 32, 1 + 3 * ns, seed=2)
+    ones = torch.ones(1 + 3 * ns, dtype=torch.float32, device="cuda")
+    zeros = torch.zeros_like(ones)
+    norm = dict(in_mean=mean, in_std=std, out_mean=zeros + np.log(1e-7), out_std=ones)
+    h0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    z0 = torch.empty((3 * ns, n), dtype=torch.float64, device="cuda")
+    net.predict(ns, Y, T, P, 1e-4, norm, h0=h0, z0=z0)
+    h0n = h0.cpu().numpy()
+    assert np.all(np.isfinite(h0n)) and np.all(h0n <= 1e-4) and np.all(h0n >= 1e-14)
+    assert np.all(np.isfinite(z0.cpu().numpy()))

@@ -368,3 +368,79 @@ def test_table_exp_against_cuda_and_libm(h2):
         ulp = np.abs(yg[fin] - ref[fin]) / np.spacing(ref[fin])
         assert ulp.max() <= 2.0, ulp.max()
     assert yg[-1] == ref_cuda[-1] and yg[-2] == ref_cuda[-2]   # outside |x|<=700: library exp
+
+
+# ----------------------------------------------------------------------------
+# queue refill granularity and the autotuner
+# ----------------------------------------------------------------------------
+
+def test_refill_batches_give_identical_results(h2):
+    mech, mg, st = h2
+    st = st.subset(np.arange(700))
+    ref = run_gpu(mg, st, 1e-5, layout="queue", queue_refill=1)
+    for r in (4, 13, 32):
+        got = run_gpu(mg, st, 1e-5, layout="queue", queue_refill=r)
+        for a, b in zip(ref, got):
+            np.testing.assert_array_equal(a, b)
+    with pytest.raises(kin.KinError):
+        run_gpu(mg, st, 1e-5, layout="queue", queue_refill=33)
+
+
+def test_autotuner_returns_a_valid_choice_and_keeps_inputs(h2):
+    mech, mg, st = h2
+    Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
+    best, secs = mg.autotune(Y, T, P, 1e-5, lu_fp32=True)
+    assert best["layout"] in ("plain", "queue") and best["block"] in (32, 64)
+    assert len(secs) == 8 and all(s > 0 for s in secs)
+    np.testing.assert_array_equal(Y.cpu().numpy(), st.Y)
+    np.testing.assert_array_equal(T.cpu().numpy(), st.T)
+    a = run_gpu(mg, st, 1e-5, lu_fp32=True, **{k: v for k, v in best.items() if k != "grid_per_sm"})
+    b = run_gpu(mg, st, 1e-5, lu_fp32=True, layout="plain")
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+
+# ----------------------------------------------------------------------------
+# WARP layout (one state per warp)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lu_fp32", [False, True])
+def test_warp_layout_h2_parity(h2, h2_oracle, lu_fp32):
+    mech, mg, st = h2
+    Yo, To, co = h2_oracle
+    Yg, Tg, cg, sg = run_gpu(mg, st, 1e-6, layout="warp", lu_fp32=lu_fp32)
+    assert np.all(sg == 0)
+    eT, eY, per = parity(Yg, Tg, Yo, To)
+    if not lu_fp32:
+        assert np.mean(per <= RTOL_PARITY) >= 0.99, (eT, eY)
+        same = np.all(cg[:, :7] == co[:, :7], axis=1)
+        assert same.mean() >= 0.95, same.mean()
+    E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), np.concatenate([To[None], Yo[:-1]]))
+    assert E.max() < 50.0 and np.median(E) < 1.0
+
+
+def test_warp_layout_ch4_parity(ch4):
+    mech, mg, st = ch4
+    st = st.subset(np.arange(64))
+    Yo, To, co = O.integrate(mech, st, 1e-6)
+    Yg, Tg, cg, sg = run_gpu(mg, st, 1e-6, layout="warp")
+    assert np.all(sg == 0)
+    eT, eY, per = parity(Yg, Tg, Yo, To)
+    assert np.mean(per <= RTOL_PARITY) >= 0.95, (eT, eY)
+    Yf, Tf, cf, sf = run_gpu(mg, st, 1e-6, layout="warp", lu_fp32=True)
+    assert np.all(sf == 0)
+    E = O.error_norm(np.concatenate([Tf[None], Yf[:-1]]), np.concatenate([To[None], Yo[:-1]]))
+    assert np.median(E) < 1.0 and E.max() < 50.0, (np.median(E), E.max())
+
+
+def test_warp_layout_fd_jacobian_and_edge_sizes(ch4):
+    mech, mg, st = ch4
+    for n in (1, 5, 33):
+        sub = st.subset(np.arange(n))
+        Yo, To, co = O.integrate(mech, sub, 1e-6, jac_kind=1)
+        Yg, Tg, cg, sg = run_gpu(mg, sub, 1e-6, layout="warp", jac_fd=True)
+        assert np.all(sg == 0)
+        eT, eY, per = parity(Yg, Tg, Yo, To)
+        assert eT <= RTOL_PARITY
+        E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), np.concatenate([To[None], Yo[:-1]]))
+        assert E.max() < 1.0, E.max()
