@@ -39,11 +39,17 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dt", type=float, default=1e-4)
-    p.add_argument("--layout", default="auto", choices=["auto", "plain", "queue"])
+    p.add_argument("--workload", default=WORKLOAD,
+                   help="a named synthetic workload (synth.WORKLOADS); the metric's is the default")
+    p.add_argument("--layout", default="auto", choices=["auto", "plain", "queue", "warp"])
+    p.add_argument("--jac", default="analytic", choices=["analytic", "fd"],
+                   help="analytical or finite-difference Jacobian")
     p.add_argument("--fp32", type=int, default=1, help="FP32 Newton matrices (1) or FP64 (0)")
     p.add_argument("--n", type=int, default=0, help="states (0 = the workload's 2^20)")
     p.add_argument("--no-extras", action="store_true", help="skip the comparison legs")
     p.add_argument("--cpu-sample", type=int, default=2048)
+    p.add_argument("--graph", type=int, default=1,
+                   help="replay the integration as a captured CUDA graph (1) or call it (0)")
     return p.parse_args()
 
 
@@ -145,7 +151,7 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    mech, st, _ = synth.workload(WORKLOAD, n=args.n or None)
+    mech, st, _ = synth.workload(args.workload, n=args.n or None)
     n = st.n
     mg = kin.Mechanism(mech)
     Y0 = torch.from_numpy(st.Y).cuda()
@@ -160,36 +166,45 @@ def run_ours(args, rank, world):
         # autotuner (kin_autotune) on a 2^18-state prefix: layout, block, refill batch
         m = min(n, 1 << 18)
         best, secs = mg.autotune(Y0[:, :m].contiguous(), T0[:m].contiguous(), P[:m].contiguous(),
-                                 args.dt, RTOL, ATOL, stream=stream, lu_fp32=bool(args.fp32))
+                                 args.dt, RTOL, ATOL, stream=stream, lu_fp32=bool(args.fp32),
+                                 jac_fd=args.jac == "fd")
         tune = {"states": m, "best": best, "candidate_seconds": [round(x, 4) for x in secs]}
         opt = dict(layout=best["layout"], block=best["block"], queue_refill=best["queue_refill"],
-                   lu_fp32=bool(args.fp32))
+                   lu_fp32=bool(args.fp32), jac_fd=args.jac == "fd")
     else:
-        opt = dict(layout=args.layout, lu_fp32=bool(args.fp32))
+        opt = dict(layout=args.layout, lu_fp32=bool(args.fp32), jac_fd=args.jac == "fd")
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def one(dt, o, timed):
+    graph = None
+    if args.graph:
+        # one memset node + one integration kernel node, replayed each step
+        graph = mg.capture(Y, T, P, args.dt, RTOL, ATOL, **opt)
+
+    def one(dt, o, timed, g=None):
         Y.copy_(Y0)
         T.copy_(T0)
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mg.integrate(Y, T, P, dt, RTOL, ATOL, stream=stream, **o)
+        if g is not None:
+            g.replay()
+        else:
+            mg.integrate(Y, T, P, dt, RTOL, ATOL, stream=stream, **o)
         e1.record(stream)
         e1.synchronize()
         return e0.elapsed_time(e1) / 1e3
 
     for _ in range(args.warmup):
-        one(args.dt, opt, False)
+        one(args.dt, opt, False, graph)
     barrier()
     clk = ClockSampler(torch.cuda.current_device())
     clk.start()
     wall0 = time.perf_counter()
-    times = [one(args.dt, opt, True) for _ in range(args.steps)]
+    times = [one(args.dt, opt, True, graph) for _ in range(args.steps)]
     barrier()
     wall = time.perf_counter() - wall0
     clocks = clk.stop()
@@ -252,10 +267,10 @@ def run_ours(args, rank, world):
                 f64=f64, f32=f32, n=n, mech=mech, st=st, extras=out)
 
 
-def cpu_baseline(sample, dt):
+def cpu_baseline(sample, dt, workload=WORKLOAD):
     from oracle import oracle as O
     from paper_1607_03884_gb300 import synth
-    mech, st, _ = synth.workload(WORKLOAD)
+    mech, st, _ = synth.workload(workload)
     rng = np.random.default_rng(1)
     idx = np.sort(rng.choice(st.n, size=sample, replace=False))
     sub = st.subset(idx)
@@ -263,8 +278,36 @@ def cpu_baseline(sample, dt):
     O.integrate(mech, sub, dt, rtol=RTOL, atol=ATOL)
     el = time.perf_counter() - t0
     return {"value": sample / el, "unit": "states/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{sample} states drawn (seed 1) from the {WORKLOAD} workload, dt={dt:g}",
+            "sample": f"{sample} states drawn (seed 1) from the {workload} workload, dt={dt:g}",
             "seconds": el}
+
+
+def kernel_digest():
+    """Digest of the CUDA sources: a traffic figure taken from an older build is void."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1607_03884_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(key, n):
+    """DRAM bytes (read + write) of one integration launch over n states, from
+    the ncu capture summarised in profiles/dram_traffic.json (bytes per state,
+    scaled by states), or None when that capture is of other kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = rec.get("kernels", {}).get(key)
+    if not e or rec.get("sources_digest") != kernel_digest():
+        return None
+    return float(e["bytes_per_state"]) * n
 
 
 def peaks():
@@ -291,7 +334,7 @@ def main():
             return
         reps = []
         for _ in range(args.warmup + args.steps):
-            reps.append(cpu_baseline(max(64, args.cpu_sample // 4), args.dt))
+            reps.append(cpu_baseline(max(64, args.cpu_sample // 4), args.dt, args.workload))
         vals = [r["value"] for r in reps[args.warmup:]]
         v = float(np.mean(vals))
         cb = dict(reps[-1])
@@ -301,7 +344,7 @@ def main():
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * cb["seconds"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dt": args.dt, "rtol": RTOL, "atol": ATOL,
+            "config": {"workload": args.workload, "dt": args.dt, "rtol": RTOL, "atol": ATOL,
                        "sample": cb["sample"]},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0,
@@ -314,27 +357,30 @@ def main():
     t = r["t_step"]
     a64 = r["f64"] / t / 1e12
     roof = {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": a64 / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": a64 / FP64_PEAK_TFLOPS,
+            "traffic": dram_traffic(f"{r['extras']['opt'].get('layout')}:"
+                                    f"{'f32' if args.fp32 else 'f64'}", r["n"]),
             "pipe": "fp64", "kernel": f"k_integrate_{r['extras']['opt'].get('layout')}",
             "peak_source": "152 SMs x 2 FP64 FMA/clk x 2.07 GHz (unit count measured)",
             "fp32_tflops": r["f32"] / t / 1e12}
-    cb = cpu_baseline(args.cpu_sample, args.dt) if not args.no_extras else None
+    cb = cpu_baseline(args.cpu_sample, args.dt, args.workload) if not args.no_extras else None
     ex = r["extras"]
     line = {
         "metric": METRIC, "value": r["value"], "unit": "states/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if args.fp32 else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "states": r["n"], "species": r["mech"].ns,
+        "config": {"workload": args.workload, "states": r["n"], "species": r["mech"].ns,
                    "reactions": r["mech"].nr, "dt": args.dt, "rtol": RTOL, "atol": ATOL,
                    "layout": ex["opt"].get("layout"), "block": ex["opt"].get("block", 0),
                    "queue_refill": ex["opt"].get("queue_refill", 0), "autotune": ex.get("tune"),
-                   "newton_matrices": "fp32" if args.fp32 else "fp64",
+                   "newton_matrices": "fp32" if args.fp32 else "fp64", "jacobian": args.jac,
                    "l2": "flushed (256 MiB write) and inputs restored before each timed step"},
         "roofline": roof,
         "cpu_baseline": cb,
         "e2e": ex.get("e2e"),
         "gpu_launches": args.steps,
+        "graph": bool(args.graph),
         "clocks": r["clocks"],
         "plain_fp64_states_per_s": ex.get("plain_fp64_states_per_s"),
         "vs_plain_fp64": (r["value"] / world / ex["plain_fp64_states_per_s"]

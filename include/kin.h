@@ -119,7 +119,9 @@ typedef struct {
   int32_t queue_refill;  /* QUEUE: a warp refills once at least this many of its
                             lanes are idle (1..32), taking that many states
                             with one atomic; 0 = 1                         (0) */
-  int32_t reserved;      /* must be 0                                      (0) */
+  int32_t stop_after;    /* > 0: end a state after this many accepted steps
+                            (it is returned at the time reached, status 0);
+                            used to collect first steps for training     (0) */
   const double *h0;      /* dev [n] first internal step per state, or NULL  */
   const double *z0;      /* dev [3*ns][n] first-step stage guesses, or NULL */
   double *h_first;       /* dev [n] out: first accepted step, or NULL       */
@@ -176,13 +178,16 @@ int kin_integrate_host(kin_mech *m, double *Y, double *T, const double *P, int64
 
 /* Autotuner: time candidate launch configurations on the caller's states
  * (Y, T, P dev, n states; copied, the inputs are not modified) and return the
- * fastest in *best.  Candidates: PLAIN with 64 and 32 threads per block;
- * QUEUE with 64 threads and refill batches 1, 4, 8, 16, 32 threads and
- * refill 1 (so max_candidates <= 8).  The other option fields (precision,
- * Jacobian, limits, h0/z0 must be NULL) come from base (NULL = defaults).
- * seconds: host [max_candidates] or NULL, each candidate's device time in
- * that order.  Allocates and frees temporary device copies of the states.
- * Synchronises the stream. */
+ * fastest in *best.  Candidates for ns <= 16: PLAIN with 64 and 32 threads
+ * per block; QUEUE with 64 threads and refill batches 1, 4, 8, 16, 32; QUEUE
+ * with 32 threads and refill 1; WARP (9 in all; the first max_candidates are
+ * timed).  For ns > 16 the per-thread matrices do not fit on chip and WARP
+ * is returned without timing.  The other option fields (precision,
+ * Jacobian, limits; h0/z0 must be NULL) come from base (NULL = defaults).
+ * seconds: host [max_candidates] or NULL, each timed candidate's device time
+ * in that order (entries past the timed ones are not written).  Allocates
+ * and frees temporary device copies of the states.  Synchronises the
+ * stream. */
 int kin_autotune(kin_mech *m, const double *Y, const double *T, const double *P, int64_t n,
                  double dt, double rtol, double atol, const kin_options *base, kin_options *best,
                  double *seconds, int32_t max_candidates, void *stream);

@@ -193,7 +193,7 @@ extern "C" int kin_options_default(kin_options *o) {
   o->grid_per_sm = 0;
   o->transform_tol = 1;
   o->queue_refill = 0;
-  o->reserved = 0;
+  o->stop_after = 0;
   return KIN_OK;
 }
 
@@ -449,7 +449,7 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   if (o.layout != KIN_LAYOUT_PLAIN && o.layout != KIN_LAYOUT_QUEUE && o.layout != KIN_LAYOUT_WARP)
     return KIN_ERR_INVALID_ARG;
   if (o.nit < 1 || o.nit > 50 || o.max_steps < 1) return KIN_ERR_INVALID_ARG;
-  if (o.queue_refill < 0 || o.queue_refill > 32 || o.reserved != 0) return KIN_ERR_INVALID_ARG;
+  if (o.queue_refill < 0 || o.queue_refill > 32 || o.stop_after < 0) return KIN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   m->last_stream = st;
   KIN_CUDA_TRY(cudaMemsetAsync(m->d_totals, 0, sizeof(unsigned long long) * 16, st));
@@ -481,6 +481,7 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   a.rp.z0 = o.z0;
   a.rp.h_first = o.h_first;
   a.rp.z_first = o.z_first;
+  a.rp.stop_after = o.stop_after;
   a.refill_min = o.queue_refill > 0 ? o.queue_refill : 1;
   int dev = 0, sms = 0;
   KIN_CUDA_TRY(cudaGetDevice(&dev));
@@ -611,13 +612,25 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
   struct Cand {
     int layout, block, refill;
   };
-  const Cand cands[] = {{KIN_LAYOUT_PLAIN, 64, 0}, {KIN_LAYOUT_PLAIN, 32, 0},
+  // thread layouts only while the per-thread matrices stay on chip (N <= 16);
+  // beyond that a state per warp is the one layout that fits
+  const Cand small[] = {{KIN_LAYOUT_PLAIN, 64, 0}, {KIN_LAYOUT_PLAIN, 32, 0},
                         {KIN_LAYOUT_QUEUE, 64, 1}, {KIN_LAYOUT_QUEUE, 64, 4},
                         {KIN_LAYOUT_QUEUE, 64, 8}, {KIN_LAYOUT_QUEUE, 64, 16},
-                        {KIN_LAYOUT_QUEUE, 64, 32}, {KIN_LAYOUT_QUEUE, 32, 1}};
-  const int nc = (int)(sizeof cands / sizeof cands[0]) < max_candidates
-                     ? (int)(sizeof cands / sizeof cands[0])
-                     : max_candidates;
+                        {KIN_LAYOUT_QUEUE, 64, 32}, {KIN_LAYOUT_QUEUE, 32, 1},
+                        {KIN_LAYOUT_WARP, 0, 0}};
+  const Cand large[] = {{KIN_LAYOUT_WARP, 0, 0}};
+  const bool is_small = m->L.ns <= 16;
+  const Cand *cands = is_small ? small : large;
+  const int ncand = is_small ? (int)(sizeof small / sizeof small[0]) : 1;
+  const int nc = ncand < max_candidates ? ncand : max_candidates;
+  if (nc == 1) {
+    *best = b;
+    best->layout = cands[0].layout;
+    best->block = cands[0].block;
+    best->queue_refill = cands[0].refill;
+    return KIN_OK;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int ns = m->L.ns;
   double *y = nullptr, *t = nullptr;

@@ -43,6 +43,7 @@ struct RadauParams {
   const double *z0;    // [3N][n] or null
   double *h_first;     // [n] or null
   double *z_first;     // [3N][n] or null
+  int stop_after;      // > 0: finish a state after this many accepted steps
 };
 
 template <int MAXN, typename LT>
@@ -534,7 +535,7 @@ __device__ bool radau_step(const MechView &m, double P, Work<MAXN, LT> &w, StepS
       }
   }
   accept_update(N, w, p);
-  if (s.last) return true;
+  if (s.last || (p.stop_after > 0 && s.naccpt >= p.stop_after)) return true;
   // f0 at the new point; the Jacobian there too when the reuse rule will ask
   // for it (slow contraction), sharing the rates
   const bool wantJ = !FDJ && s.theta > THET;

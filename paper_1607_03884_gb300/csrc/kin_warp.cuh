@@ -897,7 +897,7 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P, WSt
       w.scal.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
     }
   }
-  if (s.last) return true;
+  if (s.last || (p.stop_after > 0 && s.naccpt >= p.stop_after)) return true;
   const bool wantJ = !FDJ && s.theta > THET;
   if (warp_chem<LT>(m, b, P, w.y, w.f0, wantJ)) {
     s.status = 4;

@@ -48,8 +48,8 @@ class Options(C.Structure):
     _fields_ = [("layout", C.c_int32), ("lu_fp32", C.c_int32), ("jac_fd", C.c_int32),
                 ("max_steps", C.c_int32), ("nit", C.c_int32), ("block", C.c_int32),
                 ("grid_per_sm", C.c_int32), ("transform_tol", C.c_int32),
-                ("queue_refill", C.c_int32), ("reserved", C.c_int32), ("h0", C.c_void_p), ("z0", C.c_void_p), ("h_first", C.c_void_p),
-                ("z_first", C.c_void_p)]
+                ("queue_refill", C.c_int32), ("stop_after", C.c_int32), ("h0", C.c_void_p),
+                ("z0", C.c_void_p), ("h_first", C.c_void_p), ("z_first", C.c_void_p)]
 
 
 _lib = None
@@ -125,8 +125,8 @@ def _stream(stream):
 
 
 def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7, block=0,
-            grid_per_sm=0, transform_tol=True, queue_refill=0, h0=None, z0=None, h_first=None,
-            z_first=None):
+            grid_per_sm=0, transform_tol=True, queue_refill=0, stop_after=0, h0=None, z0=None,
+            h_first=None, z_first=None):
     o = Options()
     _check(lib().kin_options_default(C.byref(o)), "kin_options_default")
     o.layout = {"plain": LAYOUT_PLAIN, "queue": LAYOUT_QUEUE, "warp": LAYOUT_WARP}[layout] \
@@ -140,6 +140,7 @@ def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7
     o.grid_per_sm = int(grid_per_sm)
     o.transform_tol = int(bool(transform_tol))
     o.queue_refill = int(queue_refill)
+    o.stop_after = int(stop_after)
     o.h0, o.z0, o.h_first, o.z_first = _ptr(h0), _ptr(z0), _ptr(h_first), _ptr(z_first)
     return o
 
@@ -221,6 +222,20 @@ class Mechanism:
                                     _ptr(counters), _stream(stream))
         _check(rc, "kin_integrate_ex")
 
+    def capture(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, status=None, counters=None, **opt):
+        """Capture one kin_integrate_ex call into a CUDA graph (torch.cuda.CUDAGraph).
+
+        Each replay() integrates the same buffers in place over dt with the
+        launch configuration fixed at capture: one memset node (the batch
+        totals) and one integration kernel node.  Capture itself runs nothing.
+        """
+        import torch
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            self.integrate(Y, T, P, dt, rtol, atol, status=status, counters=counters,
+                           stream=torch.cuda.current_stream(), **opt)
+        return g
+
     def integrate_default(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, stream=None):
         """kin_integrate: the default options."""
         n = int(T.shape[0])
@@ -241,11 +256,12 @@ class Mechanism:
         """kin_autotune: returns (best options as a dict, list of candidate seconds)."""
         b = options(**base)
         best = Options()
-        secs = np.zeros(8)
+        secs = np.full(16, np.nan)
         rc = lib().kin_autotune(self.handle, _ptr(Y), _ptr(T), _ptr(P), int(T.shape[0]), float(dt),
                                 float(rtol), float(atol), C.byref(b), C.byref(best),
-                                secs.ctypes.data, 8, _stream(stream))
+                                secs.ctypes.data, 16, _stream(stream))
         _check(rc, "kin_autotune")
+        secs = secs[~np.isnan(secs)]
         layout = {LAYOUT_PLAIN: "plain", LAYOUT_QUEUE: "queue", LAYOUT_WARP: "warp"}[best.layout]
         return dict(layout=layout, block=best.block, queue_refill=best.queue_refill,
                     grid_per_sm=best.grid_per_sm), secs.tolist()

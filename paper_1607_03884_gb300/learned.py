@@ -38,8 +38,8 @@ class Predictor:
         return h0, z0
 
 
-def first_step_targets(mg, states, dt, rtol=1e-6, atol=1e-10, max_attempts=12, lu_fp32=True,
-                       chunk=1 << 18):
+def first_step_targets(mg, states, dt, rtol=1e-6, atol=1e-10, max_attempts=60, lu_fp32=True,
+                       chunk=1 << 18, layout="plain"):
     """(mask, h, z) on the device: the largest-accepted first step and its
     converged stages for each state (mask: the state produced both)."""
     import torch
@@ -55,13 +55,13 @@ def first_step_targets(mg, states, dt, rtol=1e-6, atol=1e-10, max_attempts=12, l
         h_try = torch.full((m,), float(dt), dtype=torch.float64, device="cuda")
         h1 = torch.zeros(m, dtype=torch.float64, device="cuda")
         mg.integrate(Y.clone(), T.clone(), P, dt, rtol, atol, h0=h_try, h_first=h1,
-                     max_steps=max_attempts, lu_fp32=lu_fp32)
+                     max_steps=max_attempts, stop_after=1, lu_fp32=lu_fp32, layout=layout)
         good = h1 > 0
         h_use = torch.where(good, h1, h_try)
         h2 = torch.zeros(m, dtype=torch.float64, device="cuda")
         z2 = torch.zeros((3 * N, m), dtype=torch.float64, device="cuda")
         mg.integrate(Y.clone(), T.clone(), P, dt, rtol, atol, h0=h_use, h_first=h2, z_first=z2,
-                     max_steps=max_attempts, lu_fp32=lu_fp32)
+                     max_steps=max_attempts, stop_after=1, lu_fp32=lu_fp32, layout=layout)
         good = good & (h2 > 0)
         hs.append(h2)
         zs.append(z2)
@@ -70,12 +70,18 @@ def first_step_targets(mg, states, dt, rtol=1e-6, atol=1e-10, max_attempts=12, l
 
 
 def train(mech, mg, states, dt, *, width=256, epochs=4, batch=4096, lr=2e-3, seed=0,
-          precision="bf16", rtol=1e-6, atol=1e-10, log=None):
-    """Generate targets with the integrator and train a predictor on them."""
+          precision="bf16", rtol=1e-6, atol=1e-10, layout="plain", h_weight=None, log=None):
+    """Generate targets with the integrator and train a predictor on them.
+
+    The loss is the mean squared error of the standardised outputs; the
+    first-step output is given the weight of all stage outputs together
+    (h_weight, default 3N) by shrinking its standardisation scale, since it
+    is the output that changes the integration most.
+    """
     import torch
     ns = mech.ns
     din, dout = 3 + ns, 1 + 3 * ns
-    mask, h, z = first_step_targets(mg, states, dt, rtol, atol)
+    mask, h, z = first_step_targets(mg, states, dt, rtol, atol, layout=layout)
     idx = torch.nonzero(mask).flatten()
     Y = torch.from_numpy(states.Y).cuda()[:, idx].contiguous()
     T = torch.from_numpy(states.T).cuda()[idx].contiguous()
@@ -91,6 +97,8 @@ def train(mech, mg, states, dt, *, width=256, epochs=4, batch=4096, lr=2e-3, see
             for k, d in (("in_mean", din), ("in_std", din), ("out_mean", dout), ("out_std", dout))}
     kin.moments(X, norm["in_mean"], norm["in_std"])
     kin.moments(Tg, norm["out_mean"], norm["out_std"])
+    w = float(h_weight if h_weight is not None else 3 * ns)
+    norm["out_std"][0:1] /= w ** 0.5
     Xs = torch.empty_like(X)
     kin.features(ns, Y, T, P, dt, Xs, norm["in_mean"], norm["in_std"])
     Ts = torch.empty_like(Tg)

@@ -261,6 +261,54 @@ def test_first_step_outputs_and_inputs(h2):
     assert np.abs(T2.cpu().numpy() - T.cpu().numpy()).max() / 3000 < 1e-5
 
 
+def test_stop_after_first_accepted_step(h2):
+    """stop_after=1 ends every state right after its first accepted step: the
+    first step and stages equal those of the full run, in every layout."""
+    mech, mg, st = h2
+    st = st.subset(np.arange(70))
+    N, n = mech.ns, st.n
+    for layout in ("plain", "queue", "warp"):
+        out = []
+        for stop in (0, 1):
+            hf = torch.zeros(n, dtype=torch.float64, device="cuda")
+            zf = torch.zeros((3 * N, n), dtype=torch.float64, device="cuda")
+            Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
+            cnt = torch.zeros((8, n), dtype=torch.int32, device="cuda")
+            status = torch.zeros(n, dtype=torch.int32, device="cuda")
+            mg.integrate(Y, T, P, 1e-4, counters=cnt, status=status, h_first=hf, z_first=zf,
+                         stop_after=stop, layout=layout)
+            torch.cuda.synchronize()
+            out.append((hf.cpu().numpy(), zf.cpu().numpy(), cnt.cpu().numpy(),
+                        status.cpu().numpy()))
+        (h_a, z_a, c_a, s_a), (h_b, z_b, c_b, s_b) = out
+        assert np.all(s_b == 0) and np.all(c_b[1] == 1)
+        assert np.all(c_a[1] >= 1) and c_a[1].sum() > c_b[1].sum()
+        np.testing.assert_array_equal(h_b, h_a)
+        np.testing.assert_array_equal(z_b, z_a)
+    with pytest.raises(kin.KinError):
+        run_gpu(mg, st, 1e-4, stop_after=-1)
+
+
+def test_graph_capture_replays_the_integration(h2):
+    """A captured integration replays to the same bits as the direct call."""
+    mech, mg, st = h2
+    st = st.subset(np.arange(300))
+    Yd, Td, _, _ = run_gpu(mg, st, 1e-5, layout="plain", lu_fp32=True)
+    Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
+    Y0, T0 = Y.clone(), T.clone()
+    g = mg.capture(Y, T, P, 1e-5, layout="plain", lu_fp32=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(T.cpu().numpy(), st.T)   # capture ran nothing
+    for _ in range(2):
+        Y.copy_(Y0)
+        T.copy_(T0)
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(Y.cpu().numpy(), Yd)
+        np.testing.assert_array_equal(T.cpu().numpy(), Td)
+    assert mg.stats()["naccpt"] > 0
+
+
 def test_edge_sizes_and_ragged_tail(h2):
     mech, mg, st = h2
     for n in (0, 1, 31, 33, 65, 130):
@@ -390,13 +438,26 @@ def test_autotuner_returns_a_valid_choice_and_keeps_inputs(h2):
     mech, mg, st = h2
     Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
     best, secs = mg.autotune(Y, T, P, 1e-5, lu_fp32=True)
-    assert best["layout"] in ("plain", "queue") and best["block"] in (32, 64)
-    assert len(secs) == 8 and all(s > 0 for s in secs)
+    assert best["layout"] in ("plain", "queue", "warp")
+    assert best["layout"] == "warp" or best["block"] in (32, 64)
+    assert len(secs) == 9 and all(s > 0 for s in secs)
     np.testing.assert_array_equal(Y.cpu().numpy(), st.Y)
     np.testing.assert_array_equal(T.cpu().numpy(), st.T)
     a = run_gpu(mg, st, 1e-5, lu_fp32=True, **{k: v for k, v in best.items() if k != "grid_per_sm"})
     b = run_gpu(mg, st, 1e-5, lu_fp32=True, layout="plain")
-    np.testing.assert_array_equal(a[1], b[1])
+    if best["layout"] == "warp":
+        eT, eY, _ = parity(a[0], a[1], b[0], b[1])
+        assert eT <= RTOL_PARITY and eY <= RTOL_PARITY
+    else:   # PLAIN and QUEUE run the same step code: the same bits
+        np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_autotuner_large_mechanism_returns_warp_untimed(ch4):
+    mech, mg, st = ch4
+    sub = st.subset(np.arange(64))
+    Y, T, P = dev(sub.Y), dev(sub.T), dev(sub.P)
+    best, secs = mg.autotune(Y, T, P, 1e-6, lu_fp32=True)
+    assert best["layout"] == "warp" and len(secs) == 0
 
 
 
