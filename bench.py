@@ -42,12 +42,16 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD,
                    help="a named synthetic workload (synth.WORKLOADS); the metric's is the default")
     p.add_argument("--layout", default="auto", choices=["auto", "plain", "queue", "warp"])
+    p.add_argument("--lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
+                   help="lanes per state for --layout warp (0 = 32)")
     p.add_argument("--jac", default="analytic", choices=["analytic", "fd"],
                    help="analytical or finite-difference Jacobian")
     p.add_argument("--fp32", type=int, default=1, help="FP32 Newton matrices (1) or FP64 (0)")
     p.add_argument("--n", type=int, default=0, help="states (0 = the workload's 2^20)")
     p.add_argument("--no-extras", action="store_true", help="skip the comparison legs")
     p.add_argument("--cpu-sample", type=int, default=2048)
+    p.add_argument("--order", default="none", choices=["none", "heuristic"],
+                   help="order the states by the starting-step heuristic inside each step")
     p.add_argument("--graph", type=int, default=1,
                    help="replay the integration as a captured CUDA graph (1) or call it (0)")
     return p.parse_args()
@@ -170,9 +174,10 @@ def run_ours(args, rank, world):
                                  jac_fd=args.jac == "fd")
         tune = {"states": m, "best": best, "candidate_seconds": [round(x, 4) for x in secs]}
         opt = dict(layout=best["layout"], block=best["block"], queue_refill=best["queue_refill"],
-                   lu_fp32=bool(args.fp32), jac_fd=args.jac == "fd")
+                   lanes=best["lanes"], lu_fp32=bool(args.fp32), jac_fd=args.jac == "fd")
     else:
-        opt = dict(layout=args.layout, lu_fp32=bool(args.fp32), jac_fd=args.jac == "fd")
+        opt = dict(layout=args.layout, lu_fp32=bool(args.fp32), jac_fd=args.jac == "fd",
+                   lanes=args.lanes)
 
     def barrier():
         if dist is not None:
@@ -182,9 +187,13 @@ def run_ours(args, rank, world):
     graph = None
     if args.graph:
         # one memset node + one integration kernel node, replayed each step
-        graph = mg.capture(Y, T, P, args.dt, RTOL, ATOL, **opt)
+        graph = mg.capture(Y, T, P, args.dt, RTOL, ATOL,
+                           order_by=None if args.order == "none" else args.order, **opt)
+    ordered = args.order != "none"
+    key_buf = torch.empty(n, dtype=torch.float64, device="cuda")
+    order_buf = torch.empty(n, dtype=torch.int32, device="cuda")
 
-    def one(dt, o, timed, g=None):
+    def one(dt, o, timed, g=None, ordered=False):
         Y.copy_(Y0)
         T.copy_(T0)
         flush.zero_()
@@ -192,6 +201,9 @@ def run_ours(args, rank, world):
         e0.record(stream)
         if g is not None:
             g.replay()
+        elif ordered:
+            mg.order_states(Y, T, P, RTOL, ATOL, key=key_buf, order=order_buf, stream=stream)
+            mg.integrate(Y, T, P, dt, RTOL, ATOL, stream=stream, order=order_buf, **o)
         else:
             mg.integrate(Y, T, P, dt, RTOL, ATOL, stream=stream, **o)
         e1.record(stream)
@@ -199,12 +211,12 @@ def run_ours(args, rank, world):
         return e0.elapsed_time(e1) / 1e3
 
     for _ in range(args.warmup):
-        one(args.dt, opt, False, graph)
+        one(args.dt, opt, False, graph, ordered)
     barrier()
     clk = ClockSampler(torch.cuda.current_device())
     clk.start()
     wall0 = time.perf_counter()
-    times = [one(args.dt, opt, True, graph) for _ in range(args.steps)]
+    times = [one(args.dt, opt, True, graph, ordered) for _ in range(args.steps)]
     barrier()
     wall = time.perf_counter() - wall0
     clocks = clk.stop()
@@ -235,8 +247,8 @@ def run_ours(args, rank, world):
                                       "E_p99": float(np.percentile(E, 99))}
         # dt = 1e-6 for both
         other = 1e-6 if args.dt != 1e-6 else 1e-4
-        one(other, opt, False)
-        t_o = float(np.mean([one(other, opt, True) for _ in range(2)]))
+        one(other, opt, False, None, ordered)
+        t_o = float(np.mean([one(other, opt, True, None, ordered) for _ in range(2)]))
         one(other, base_opt, False)
         t_ob = float(np.mean([one(other, base_opt, True) for _ in range(2)]))
         out["per_dt"] = {str(args.dt): {"ours": value / world, "plain_fp64": out["plain_fp64_states_per_s"]},
@@ -373,8 +385,10 @@ def main():
         "config": {"workload": args.workload, "states": r["n"], "species": r["mech"].ns,
                    "reactions": r["mech"].nr, "dt": args.dt, "rtol": RTOL, "atol": ATOL,
                    "layout": ex["opt"].get("layout"), "block": ex["opt"].get("block", 0),
-                   "queue_refill": ex["opt"].get("queue_refill", 0), "autotune": ex.get("tune"),
+                   "queue_refill": ex["opt"].get("queue_refill", 0),
+                   "lanes": ex["opt"].get("lanes", 0), "autotune": ex.get("tune"),
                    "newton_matrices": "fp32" if args.fp32 else "fp64", "jacobian": args.jac,
+                   "order": args.order,
                    "l2": "flushed (256 MiB write) and inputs restored before each timed step"},
         "roofline": roof,
         "cpu_baseline": cb,

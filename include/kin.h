@@ -97,11 +97,13 @@ enum {
                            whose state is done takes the next one from an
                            atomic work queue (answers the warp divergence of
                            Sec. 3.3: no lane waits for the slowest state) */,
-  KIN_LAYOUT_WARP = 2   /* one state per warp (ns <= 63): vectors over lanes,
-                           Newton matrices in shared memory, warp-cooperative
-                           LU and solves, rates in parallel over reactions;
-                           warps pop states from the atomic queue.  For large
-                           mechanisms (the per-block strategy of Sec. 3.3) */
+  KIN_LAYOUT_WARP = 2   /* one state per group of kin_options.lanes lanes
+                           (a whole warp: ns <= 63; 4, 8 or 16 lanes:
+                           ns <= 15): vectors over the group's lanes, Newton
+                           matrices in shared memory, group-cooperative LU
+                           and solves, rates in parallel over reactions;
+                           groups pop states from the atomic queue (the
+                           per-block strategy of Sec. 3.3) */
 };
 
 /* Integration options.  kin_options_default fills the defaults. */
@@ -126,6 +128,18 @@ typedef struct {
   const double *z0;      /* dev [3*ns][n] first-step stage guesses, or NULL */
   double *h_first;       /* dev [n] out: first accepted step, or NULL       */
   double *z_first;       /* dev [3*ns][n] out: converged first-step stages  */
+  const int32_t *order;  /* dev [n] slot -> state permutation (for example from
+                            kin_order_states), or NULL for the identity.
+                            Slot i integrates state order[i]; indices of Y,
+                            T, P, status, counters, h0, z0, h_first, z_first
+                            are state indices.  Entries outside [0, n) are
+                            skipped and make kin_get_stats return
+                            KIN_ERR_INVALID_ARG; a repeated entry integrates
+                            that state twice and leaves another untouched.
+                            n <= 2^31 - 1 with an order.              (NULL) */
+  int32_t lanes;         /* KIN_LAYOUT_WARP: lanes per state, 4, 8, 16 or 32
+                            (0 = 32).  4, 8 and 16 hold at most 15 species
+                            and place 32/lanes states in each warp      (0) */
 } kin_options;
 
 /* Per-state counters written by kin_integrate_ex when counters != NULL:
@@ -178,11 +192,12 @@ int kin_integrate_host(kin_mech *m, double *Y, double *T, const double *P, int64
 
 /* Autotuner: time candidate launch configurations on the caller's states
  * (Y, T, P dev, n states; copied, the inputs are not modified) and return the
- * fastest in *best.  Candidates for ns <= 16: PLAIN with 64 and 32 threads
+ * fastest in *best.  Candidates for ns <= 15: PLAIN with 64 and 32 threads
  * per block; QUEUE with 64 threads and refill batches 1, 4, 8, 16, 32; QUEUE
- * with 32 threads and refill 1; WARP (9 in all; the first max_candidates are
- * timed).  For ns > 16 the per-thread matrices do not fit on chip and WARP
- * is returned without timing.  The other option fields (precision,
+ * with 32 threads and refill 1; WARP with 32, 16, 8 and 4 lanes per state
+ * (12 in all; the first max_candidates are timed).  ns = 16 drops the
+ * grouped WARP forms (9).  For ns > 16 the per-thread matrices do not fit
+ * on chip and WARP (32 lanes) is returned without timing.  The other option fields (precision,
  * Jacobian, limits; h0/z0 must be NULL) come from base (NULL = defaults).
  * seconds: host [max_candidates] or NULL, each timed candidate's device time
  * in that order (entries past the timed ones are not written).  Allocates
@@ -195,8 +210,32 @@ int kin_autotune(kin_mech *m, const double *Y, const double *T, const double *P,
 /* Totals of the last kin_integrate* call on this mechanism, reduced on the
  * device: out[0..6] = sums of the KIN_CNT_* counters 0..6, out[7] = number of
  * failed states, out[8] = largest per-state step count.  Synchronises the
- * mechanism's last stream.  Returns KIN_ERR_STATE_FAILED when out[7] > 0. */
+ * mechanism's last stream.  Returns KIN_ERR_INVALID_ARG when the call's
+ * kin_options.order held entries outside [0, n) (those slots were skipped),
+ * else KIN_ERR_STATE_FAILED when out[7] > 0. */
 int kin_get_stats(kin_mech *m, int64_t *out);
+
+/* Stiffness-ordered batching.  The paper names warp divergence from differing
+ * internal step counts as the main limit of the per-thread integrator
+ * (Sec. 3.3, Sec. 4.2); grouping states of similar stiffness in a warp
+ * reduces it.  Writes to order (dev [n]) a permutation of 0..n-1 that sorts
+ * key (dev [n]) ascending, stiffest states first, by a counting sort into
+ * 4096 equal-width bins between the smallest and largest finite key (-inf
+ * first, +inf and NaN last; the order within a bin is unspecified, and the
+ * integration of a state does not depend on its slot).
+ *   key_mode KIN_KEY_STEP_HEURISTIC: the library first writes into key the
+ *     natural log of the starting-step heuristic 0.01 d0/d1 (weighted RMS
+ *     norms of y and f(y), tolerances transformed as in the integrator): one
+ *     right-hand side per state from Y, T, P (dev, as kin_integrate); a state
+ *     whose rates are not finite gets -inf.
+ *   key_mode KIN_KEY_GIVEN: key is read as given (for example the predictor's
+ *     ln h0); Y, T, P, rtol and atol are not used and may be NULL/0.
+ * n <= 2^31 - 1.  Asynchronous on stream; uses a workspace owned by the
+ * mechanism, so calls on one kin_mech must not overlap. */
+enum { KIN_KEY_GIVEN = 0, KIN_KEY_STEP_HEURISTIC = 1 };
+int kin_order_states(kin_mech *m, const double *Y, const double *T, const double *P, int64_t n,
+                     double rtol, double atol, int32_t key_mode, double *key, int32_t *order,
+                     void *stream);
 
 /* Source terms f(y) for n states (y = [T, Y_0..Y_{ns-2}], N = ns):
  * y dev [N][n], P dev [n], f dev [N][n] out.  Unit-level entry of the

@@ -284,6 +284,15 @@ int orc_radau(int n, orc_rhs_fn f, orc_jac_fn jac, void *ctx, double t0, double 
       break;
     }
     if (0.1 * fabs(h) <= fabs(x) * UROUND) {
+      /* A final step shorter than the round-off of t: the state is already
+         at t1 to round-off (the integration is over a fixed global step,
+         Sec. 2.3), so it ends there.  Any other step this short is an
+         underflow. */
+      if (last) {
+        x = t1;
+        st->h_last = hopt;
+        break;
+      }
       status = ORC_H_UNDERFLOW;
       break;
     }

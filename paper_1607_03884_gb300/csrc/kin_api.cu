@@ -29,7 +29,9 @@ struct kin_mech {
   MechLayout L;
   double *d_tab = nullptr;
   int *d_itab = nullptr;
-  unsigned long long *d_totals = nullptr;  // [0..6] sums, [7] failed, [8] max steps, [9] queue
+  unsigned long long *d_totals = nullptr;  // [0..6] sums, [7] failed, [8] max steps, [9] queue,
+                                           // [10] order entries out of range
+  void *d_order_ws = nullptr;              // kin_order_states workspace
   cudaStream_t last_stream = nullptr;
   // host-call buffers
   double *h_Y = nullptr, *h_T = nullptr, *h_P = nullptr;
@@ -117,7 +119,7 @@ int kin::ensure_constants(int dev) {
   RadauConst rc = radau_constants_host();
   int r;
   if ((r = kin_consts_16d(rc)) || (r = kin_consts_16f(rc)) || (r = kin_consts_64d(rc)) ||
-      (r = kin_consts_64f(rc)))
+      (r = kin_consts_64f(rc)) || (r = kin_consts_grpd(rc)) || (r = kin_consts_grpf(rc)))
     return r;
   g_const_done[dev] = true;
   return KIN_OK;
@@ -194,6 +196,8 @@ extern "C" int kin_options_default(kin_options *o) {
   o->transform_tol = 1;
   o->queue_refill = 0;
   o->stop_after = 0;
+  o->order = nullptr;
+  o->lanes = 0;
   return KIN_OK;
 }
 
@@ -388,7 +392,8 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
   m->L = L;
   if (cudaMalloc(&m->d_tab, sizeof(double) * L.nd) != cudaSuccess ||
       cudaMalloc(&m->d_itab, sizeof(int) * L.ni) != cudaSuccess ||
-      cudaMalloc(&m->d_totals, sizeof(unsigned long long) * 16) != cudaSuccess) {
+      cudaMalloc(&m->d_totals, sizeof(unsigned long long) * 16) != cudaSuccess ||
+      cudaMalloc(&m->d_order_ws, order_workspace_bytes()) != cudaSuccess) {
     (void)cudaGetLastError();
     kin_destroy(m);
     return KIN_ERR_NOMEM;
@@ -411,6 +416,7 @@ extern "C" void kin_destroy(kin_mech *m) {
   cudaFree(m->d_tab);
   cudaFree(m->d_itab);
   cudaFree(m->d_totals);
+  cudaFree(m->d_order_ws);
   cudaFree(m->h_Y);
   cudaFree(m->h_T);
   cudaFree(m->h_P);
@@ -421,6 +427,8 @@ extern "C" void kin_destroy(kin_mech *m) {
 
 int kin::launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t st,
                          int sms) {
+  if (o.layout == KIN_LAYOUT_WARP && o.lanes != 0 && o.lanes != 32)
+    return o.lu_fp32 ? kin_launch_grpf(a, o, st, sms) : kin_launch_grpd(a, o, st, sms);
   if (a.L.ns <= 16 && o.layout != KIN_LAYOUT_WARP)
     return o.lu_fp32 ? kin_launch_16f(a, o, st, sms) : kin_launch_16d(a, o, st, sms);
   return o.lu_fp32 ? kin_launch_64f(a, o, st, sms) : kin_launch_64d(a, o, st, sms);
@@ -450,6 +458,9 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
     return KIN_ERR_INVALID_ARG;
   if (o.nit < 1 || o.nit > 50 || o.max_steps < 1) return KIN_ERR_INVALID_ARG;
   if (o.queue_refill < 0 || o.queue_refill > 32 || o.stop_after < 0) return KIN_ERR_INVALID_ARG;
+  if (o.order && n > INT32_MAX) return KIN_ERR_INVALID_ARG;
+  if (o.lanes != 0 && o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32)
+    return KIN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   m->last_stream = st;
   KIN_CUDA_TRY(cudaMemsetAsync(m->d_totals, 0, sizeof(unsigned long long) * 16, st));
@@ -483,6 +494,7 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   a.rp.z_first = o.z_first;
   a.rp.stop_after = o.stop_after;
   a.refill_min = o.queue_refill > 0 ? o.queue_refill : 1;
+  a.order = o.order;
   int dev = 0, sms = 0;
   KIN_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != m->device) return KIN_ERR_INVALID_ARG;
@@ -508,7 +520,8 @@ extern "C" int kin_integrate_host(kin_mech *m, double *Y, double *T, const doubl
                                   int32_t *status, int32_t *counters, void *stream) {
   int rc = check_common(m, Y, T, P, n, dt, rtol, atol);
   if (rc) return rc;
-  if (opt && (opt->h0 || opt->z0 || opt->h_first || opt->z_first)) return KIN_ERR_INVALID_ARG;
+  if (opt && (opt->h0 || opt->z0 || opt->h_first || opt->z_first || opt->order))
+    return KIN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int ns = m->L.ns;
   if (n > m->h_cap) {
@@ -544,7 +557,29 @@ extern "C" int kin_get_stats(kin_mech *m, int64_t *out) {
   KIN_CUDA_TRY(cudaStreamSynchronize(m->last_stream));
   KIN_CUDA_TRY(cudaMemcpy(t, m->d_totals, sizeof t, cudaMemcpyDeviceToHost));
   for (int i = 0; i < 9; ++i) out[i] = (int64_t)t[i];
+  if (t[10] > 0) return KIN_ERR_INVALID_ARG;  // order entries outside [0, n) were skipped
   return out[7] > 0 ? KIN_ERR_STATE_FAILED : KIN_OK;
+}
+
+extern "C" int kin_order_states(kin_mech *m, const double *Y, const double *T, const double *P,
+                                int64_t n, double rtol, double atol, int32_t key_mode,
+                                double *key, int32_t *order, void *stream) {
+  if (!m || n < 0 || n > INT32_MAX) return KIN_ERR_INVALID_ARG;
+  if (key_mode != KIN_KEY_GIVEN && key_mode != KIN_KEY_STEP_HEURISTIC) return KIN_ERR_INVALID_ARG;
+  if (n == 0) return KIN_OK;
+  if (!key || !order) return KIN_ERR_INVALID_ARG;
+  const bool compute = key_mode == KIN_KEY_STEP_HEURISTIC;
+  if (compute) {
+    if (!Y || !T || !P || !(rtol > 0.0) || !(atol > 0.0)) return KIN_ERR_INVALID_ARG;
+  }
+  int dev = 0, sms = 0;
+  KIN_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != m->device) return KIN_ERR_INVALID_ARG;
+  KIN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // the integrator's default tolerance transform (Hairer-Wanner)
+  const double r = 0.1 * std::pow(rtol, 2.0 / 3.0), at = compute ? r * (atol / rtol) : 0.0;
+  return launch_order(m->L, m->d_tab, m->d_itab, Y, T, P, n, r, at, compute, key, order,
+                      m->d_order_ws, (cudaStream_t)stream, sms);
 }
 
 extern "C" int kin_rhs(kin_mech *m, const double *y, const double *P, int64_t n, double *f,
@@ -610,25 +645,27 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
   }
   if (b.h0 || b.z0 || b.h_first || b.z_first) return KIN_ERR_INVALID_ARG;
   struct Cand {
-    int layout, block, refill;
+    int layout, block, refill, lanes;
   };
   // thread layouts only while the per-thread matrices stay on chip (N <= 16);
   // beyond that a state per warp is the one layout that fits
-  const Cand small[] = {{KIN_LAYOUT_PLAIN, 64, 0}, {KIN_LAYOUT_PLAIN, 32, 0},
-                        {KIN_LAYOUT_QUEUE, 64, 1}, {KIN_LAYOUT_QUEUE, 64, 4},
-                        {KIN_LAYOUT_QUEUE, 64, 8}, {KIN_LAYOUT_QUEUE, 64, 16},
-                        {KIN_LAYOUT_QUEUE, 64, 32}, {KIN_LAYOUT_QUEUE, 32, 1},
-                        {KIN_LAYOUT_WARP, 0, 0}};
-  const Cand large[] = {{KIN_LAYOUT_WARP, 0, 0}};
+  const Cand small[] = {{KIN_LAYOUT_PLAIN, 64, 0, 0}, {KIN_LAYOUT_PLAIN, 32, 0, 0},
+                        {KIN_LAYOUT_QUEUE, 64, 1, 0}, {KIN_LAYOUT_QUEUE, 64, 4, 0},
+                        {KIN_LAYOUT_QUEUE, 64, 8, 0}, {KIN_LAYOUT_QUEUE, 64, 16, 0},
+                        {KIN_LAYOUT_QUEUE, 64, 32, 0}, {KIN_LAYOUT_QUEUE, 32, 1, 0},
+                        {KIN_LAYOUT_WARP, 0, 0, 32}, {KIN_LAYOUT_WARP, 0, 0, 16},
+                        {KIN_LAYOUT_WARP, 0, 0, 8}, {KIN_LAYOUT_WARP, 0, 0, 4}};
+  const Cand large[] = {{KIN_LAYOUT_WARP, 0, 0, 32}};
   const bool is_small = m->L.ns <= 16;
   const Cand *cands = is_small ? small : large;
-  const int ncand = is_small ? (int)(sizeof small / sizeof small[0]) : 1;
+  const int ncand = !is_small ? 1 : (m->L.ns <= 15 ? 12 : 9);
   const int nc = ncand < max_candidates ? ncand : max_candidates;
   if (nc == 1) {
     *best = b;
     best->layout = cands[0].layout;
     best->block = cands[0].block;
     best->queue_refill = cands[0].refill;
+    best->lanes = cands[0].lanes;
     return KIN_OK;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -657,6 +694,7 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
     o.layout = c.layout;
     o.block = c.block;
     o.queue_refill = c.refill;
+    o.lanes = c.lanes;
     if (cudaMemcpyAsync(y, Y, sizeof(double) * n * ns, cudaMemcpyDeviceToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(t, T, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
@@ -685,5 +723,6 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
   best->layout = cands[best_i].layout;
   best->block = cands[best_i].block;
   best->queue_refill = cands[best_i].refill;
+  best->lanes = cands[best_i].lanes;
   return KIN_OK;
 }

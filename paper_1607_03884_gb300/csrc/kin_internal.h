@@ -15,4 +15,10 @@ int build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double> &dt,
 int ensure_constants(int dev);
 // Launch the integration kernel that matches the options and species count.
 int launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms);
+// Stiffness ordering (kin_order.cu): device workspace size and launcher.
+size_t order_workspace_bytes();
+int launch_order(const MechLayout &L, const double *tab, const int *itab, const double *Y,
+                 const double *T, const double *P, int64_t n, double rtol, double atol,
+                 bool compute_key, double *key, int32_t *order, void *ws, cudaStream_t st,
+                 int sms);
 }  // namespace kin

@@ -32,8 +32,22 @@ struct KernelArgs {
   int32_t *status, *counters;
   unsigned long long *totals;
   RadauParams rp;
-  int refill_min;  // QUEUE: idle lanes of a warp that trigger a refill
+  int refill_min;        // QUEUE: idle lanes of a warp that trigger a refill
+  const int32_t *order;  // slot -> state permutation or null (identity)
 };
+
+// The state a slot carries: order[slot] when an order is given, else the
+// slot itself.  Entries outside [0, n) are skipped (-1) and counted in
+// totals[10], so a bad permutation cannot reach memory out of bounds.
+__device__ __forceinline__ int64_t state_of(const KernelArgs &a, int64_t slot) {
+  if (!a.order) return slot;
+  const int32_t s = a.order[slot];
+  if (s < 0 || (int64_t)s >= a.rp.n) {
+    atomicAdd(a.totals + 10, 1ull);
+    return -1;
+  }
+  return (int64_t)s;
+}
 
 template <int MAXN, typename LT>
 __device__ void load_state(Work<MAXN, LT> &w, const KernelArgs &a, int N, int64_t i) {
@@ -71,8 +85,10 @@ template <int MAXN, typename LT, bool FDJ>
 __global__ void __launch_bounds__(64) k_integrate_plain(KernelArgs a) {
   extern __shared__ double smem[];
   const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.rp.n) return;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= a.rp.n) return;
+  const int64_t i = state_of(a, slot);
+  if (i < 0) return;
   Work<MAXN, LT> w;
   StepState s;
   const int N = m.ns;
@@ -112,8 +128,8 @@ __global__ void __launch_bounds__(64) k_integrate_queue(KernelArgs a) {
       if (base + (unsigned long long)nidle >= (unsigned long long)n) exhausted = true;
       if (idx < 0) {
         const unsigned long long t = base + __popc(idle & ((1u << lane) - 1u));
-        if (t < (unsigned long long)n) {
-          idx = (int64_t)t;
+        if (t < (unsigned long long)n) idx = state_of(a, (int64_t)t);
+        if (idx >= 0) {
           P = a.P[idx];
           load_state(w, a, N, idx);
           if (radau_init<MAXN, LT, FDJ>(m, P, w, s, a.rp, idx)) {
@@ -130,45 +146,51 @@ __global__ void __launch_bounds__(64) k_integrate_queue(KernelArgs a) {
   }
 }
 
-// WARP layout: one state per warp, warps pop states from the atomic queue.
-template <typename LT, bool FDJ>
-__global__ void __launch_bounds__(128) k_integrate_warp(KernelArgs a) {
+// WARP layout: one state per group of L lanes; groups pop states from the
+// atomic queue.
+template <int L, typename LT, bool FDJ>
+__global__ void __launch_bounds__(128) k_integrate_lanes(KernelArgs a) {
+  using G = Grp<L>;
+  constexpr int WR = G::WR;
   extern __shared__ double smem[];
   const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
-  const int N = m.ns, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int N = m.ns, lane = G::lane(), grp = (int)(threadIdx.x / L);
   const int64_t n = a.rp.n;
   char *base = reinterpret_cast<char *>(smem) + (smem_bytes(a.L) + 15) / 16 * 16 +
-               (size_t)warp * warp_buf_bytes(N, m.nr, sizeof(LT));
-  const WarpBuf<LT> b = carve_warp_buf<LT>(base, N, m.nr);
+               (size_t)grp * warp_buf_bytes(N, m.nr, sizeof(LT), G::CAP);
+  const WarpBuf<LT> b = carve_warp_buf<LT>(base, N, m.nr, G::CAP);
   unsigned long long *queue = a.totals + 9;
-  WState w;
+  WStateT<WR> w;
   StepState s;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(queue, 1ull);
-    t = __shfl_sync(WFULL, t, 0);
+    t = G::bcast(t, 0);
     if (t >= (unsigned long long)n) break;
-    const int64_t idx = (int64_t)t;
+    int64_t idx = 0;
+    if (lane == 0) idx = state_of(a, (int64_t)t);
+    idx = G::bcast(idx, 0);
+    if (idx < 0) continue;
     const double P = a.P[idx];
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
-      const int g = lane + 32 * r;
+      const int g = lane + L * r;
       w.y.v[r] = (g == 0) ? a.T[idx] : (g < N ? a.Y[(int64_t)(g - 1) * n + idx] : 0.0);
     }
     // every attempt ends the loop or counts a step; max_steps bounds it
-    bool done = warp_init<LT, FDJ>(m, b, P, w, s, a.rp, idx);
-    while (!done) done = warp_step<LT, FDJ>(m, b, P, w, s, a.rp, idx);
+    bool done = warp_init<L, LT, FDJ>(m, b, P, w, s, a.rp, idx);
+    while (!done) done = warp_step<L, LT, FDJ>(m, b, P, w, s, a.rp, idx);
     double sum = 0.0;
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
-      const int g = lane + 32 * r;
+      const int g = lane + L * r;
       if (g == 0) a.T[idx] = w.y.v[r];
       if (g >= 1 && g < N) {
         a.Y[(int64_t)(g - 1) * n + idx] = w.y.v[r];
         sum += w.y.v[r];
       }
     }
-    sum = wsum(sum);
+    sum = G::sum(sum);
     if (lane == 0) {
       a.Y[(int64_t)(N - 1) * n + idx] = 1.0 - sum;
       if (a.status) a.status[idx] = s.status;
@@ -185,26 +207,34 @@ __global__ void __launch_bounds__(128) k_integrate_warp(KernelArgs a) {
       if (s.status) atomicAdd(a.totals + 7, 1ull);
       atomicMax(a.totals + 8, (unsigned long long)s.nstep);
     }
-    __syncwarp();
+    G::sync();
   }
 }
 
-template <typename LT, bool FDJ>
-int launch_warp(const KernelArgs &a, cudaStream_t st, int sms) {
-  const size_t tab = (smem_bytes(a.L) + 15) / 16 * 16;
-  const size_t wb = warp_buf_bytes(a.L.ns, a.L.nr, sizeof(LT));
+// Shared memory of one block of `warps` warps for L lanes per state.
+__host__ __device__ inline size_t lanes_smem_bytes(const MechLayout &L_, int lanes, int cap,
+                                                   size_t lt, int warps) {
+  return (smem_bytes(L_) + 15) / 16 * 16 +
+         (size_t)warps * (32 / lanes) * warp_buf_bytes(L_.ns, L_.nr, lt, cap);
+}
+
+template <int L, typename LT, bool FDJ>
+int launch_lanes(const KernelArgs &a, cudaStream_t st, int sms) {
+  using G = Grp<L>;
+  if (a.L.ns >= G::CAP) return KIN_ERR_UNSUPPORTED;
   const size_t budget = 227 * 1024;
-  if (tab + wb > budget) return KIN_ERR_UNSUPPORTED;
-  int warps = (int)((budget - tab) / wb);
-  if (warps > 4) warps = 4;
-  const size_t sm = tab + (size_t)warps * wb;
-  auto kern = k_integrate_warp<LT, FDJ>;
+  int warps = 4;
+  while (warps > 1 && lanes_smem_bytes(a.L, L, G::CAP, sizeof(LT), warps) > budget) --warps;
+  const size_t sm = lanes_smem_bytes(a.L, L, G::CAP, sizeof(LT), warps);
+  if (sm > budget) return KIN_ERR_UNSUPPORTED;
+  auto kern = k_integrate_lanes<L, LT, FDJ>;
   KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int per_sm = 0;
   KIN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, sm));
   if (per_sm < 1) return KIN_ERR_UNSUPPORTED;
   int64_t grid = (int64_t)sms * per_sm;
-  const int64_t need = (a.rp.n + warps - 1) / warps;
+  const int64_t per_block = (int64_t)warps * (32 / L);
+  const int64_t need = (a.rp.n + per_block - 1) / per_block;
   if (grid > need) grid = need;
   kern<<<(unsigned)grid, 32 * warps, sm, st>>>(a);
   KIN_CUDA_TRY(cudaGetLastError());
@@ -216,7 +246,7 @@ int launch_t(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms
   if (o.layout == KIN_LAYOUT_WARP) {
     if constexpr (MAXN == 64) {
       if (a.L.ns > 63) return KIN_ERR_UNSUPPORTED;
-      return launch_warp<LT, FDJ>(a, st, sms);
+      return launch_lanes<32, LT, FDJ>(a, st, sms);
     } else {
       return KIN_ERR_UNSUPPORTED;
     }
@@ -265,9 +295,32 @@ int launch_t(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms
                         int sms);                                                      \
   int kin_consts_##NAME(const RadauConst &rc);
 
+// Groups of 4, 8 or 16 lanes per state (at most 15 species) for one matrix
+// precision, in their own translation units.
+#define KIN_DEFINE_GROUP_TU(NAME, LT)                                                   \
+  int kin_launch_##NAME(const KernelArgs &a, const kin_options &o, cudaStream_t st,    \
+                        int sms) {                                                     \
+    const bool fd = o.jac_fd != 0;                                                     \
+    switch (o.lanes) {                                                                 \
+      case 4: return fd ? launch_lanes<4, LT, true>(a, st, sms)                        \
+                        : launch_lanes<4, LT, false>(a, st, sms);                      \
+      case 8: return fd ? launch_lanes<8, LT, true>(a, st, sms)                        \
+                        : launch_lanes<8, LT, false>(a, st, sms);                      \
+      case 16: return fd ? launch_lanes<16, LT, true>(a, st, sms)                      \
+                         : launch_lanes<16, LT, false>(a, st, sms);                    \
+      default: return KIN_ERR_INVALID_ARG;                                             \
+    }                                                                                  \
+  }                                                                                    \
+  int kin_consts_##NAME(const RadauConst &rc) {                                        \
+    KIN_CUDA_TRY(cudaMemcpyToSymbol(RC, &rc, sizeof rc));                              \
+    return KIN_OK;                                                                     \
+  }
+
 KIN_DECLARE_TU(16d)
 KIN_DECLARE_TU(16f)
 KIN_DECLARE_TU(64d)
 KIN_DECLARE_TU(64f)
+KIN_DECLARE_TU(grpd)
+KIN_DECLARE_TU(grpf)
 
 }  // namespace kin

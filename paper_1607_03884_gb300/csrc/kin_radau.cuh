@@ -472,7 +472,12 @@ __device__ bool radau_step(const MechView &m, double P, Work<MAXN, LT> &w, StepS
     return true;
   }
   if (0.1 * fabs(s.h) <= fabs(s.x) * UROUND) {
-    s.status = 2;
+    // a final step shorter than the round-off of t: the state is at dt to
+    // round-off and the integration ends; any other step this short underflowed
+    if (s.last)
+      s.x = p.dt;
+    else
+      s.status = 2;
     return true;
   }
   start_values(N, w, s, p, idx);

@@ -107,5 +107,6 @@ extern "C" int kin_integrate_static(const kin_mech_desc *desc, double *Y, double
   a.rp.z_first = nullptr;
   a.rp.stop_after = 0;
   a.refill_min = 1;
+  a.order = nullptr;
   return launch_dispatch(a, o, st, sms);
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libkin.so")
 KIN_OK, KIN_ERR_INVALID_ARG, KIN_ERR_CUDA, KIN_ERR_NOMEM, KIN_ERR_MECH = 0, 1, 2, 3, 4
 KIN_ERR_STATE_FAILED, KIN_ERR_UNSUPPORTED = 5, 6
 LAYOUT_PLAIN, LAYOUT_QUEUE, LAYOUT_WARP = 0, 1, 2
+KEY_GIVEN, KEY_STEP_HEURISTIC = 0, 1
 COUNTER_NAMES = ("nstep", "naccpt", "nrejct", "nfcn", "njac", "ndec", "nsol", "status")
 MAX_SPECIES = 64
 
@@ -28,7 +29,7 @@ EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integra
            "kin_integrate_static", "kin_mlp_create", "kin_mlp_destroy", "kin_mlp_num_params",
            "kin_mlp_get_params", "kin_mlp_set_params", "kin_mlp_forward", "kin_mlp_grad",
            "kin_mlp_train_step", "kin_moments", "kin_mlp_features", "kin_mlp_targets",
-           "kin_mlp_predict", "kin_autotune")
+           "kin_mlp_predict", "kin_autotune", "kin_order_states")
 
 
 class KinError(RuntimeError):
@@ -49,7 +50,8 @@ class Options(C.Structure):
                 ("max_steps", C.c_int32), ("nit", C.c_int32), ("block", C.c_int32),
                 ("grid_per_sm", C.c_int32), ("transform_tol", C.c_int32),
                 ("queue_refill", C.c_int32), ("stop_after", C.c_int32), ("h0", C.c_void_p),
-                ("z0", C.c_void_p), ("h_first", C.c_void_p), ("z_first", C.c_void_p)]
+                ("z0", C.c_void_p), ("h_first", C.c_void_p), ("z_first", C.c_void_p),
+                ("order", C.c_void_p), ("lanes", C.c_int32)]
 
 
 _lib = None
@@ -82,6 +84,7 @@ def lib():
             L.kin_exp.argtypes = [vp, vp, vp, i64, vp]
             L.kin_integrate_static.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp]
             L.kin_autotune.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp, vp, i32, vp]
+            L.kin_order_states.argtypes = [vp, vp, vp, vp, i64, d, d, i32, vp, vp, vp]
             L.kin_mlp_create.argtypes = [i32, i32, i32, i32, C.c_uint64, C.POINTER(vp)]
             L.kin_mlp_destroy.argtypes = [vp]
             L.kin_mlp_destroy.restype = None
@@ -126,7 +129,7 @@ def _stream(stream):
 
 def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7, block=0,
             grid_per_sm=0, transform_tol=True, queue_refill=0, stop_after=0, h0=None, z0=None,
-            h_first=None, z_first=None):
+            h_first=None, z_first=None, order=None, lanes=0):
     o = Options()
     _check(lib().kin_options_default(C.byref(o)), "kin_options_default")
     o.layout = {"plain": LAYOUT_PLAIN, "queue": LAYOUT_QUEUE, "warp": LAYOUT_WARP}[layout] \
@@ -142,6 +145,8 @@ def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7
     o.queue_refill = int(queue_refill)
     o.stop_after = int(stop_after)
     o.h0, o.z0, o.h_first, o.z_first = _ptr(h0), _ptr(z0), _ptr(h_first), _ptr(z_first)
+    o.order = _ptr(order)
+    o.lanes = int(lanes)
     return o
 
 
@@ -222,18 +227,34 @@ class Mechanism:
                                     _ptr(counters), _stream(stream))
         _check(rc, "kin_integrate_ex")
 
-    def capture(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, status=None, counters=None, **opt):
-        """Capture one kin_integrate_ex call into a CUDA graph (torch.cuda.CUDAGraph).
+    def capture(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, status=None, counters=None,
+                order_by=None, **opt):
+        """Capture one integration into a CUDA graph (torch.cuda.CUDAGraph).
 
         Each replay() integrates the same buffers in place over dt with the
         launch configuration fixed at capture: one memset node (the batch
-        totals) and one integration kernel node.  Capture itself runs nothing.
+        totals) and one integration kernel node.  With order_by="heuristic"
+        the graph first orders the states by the starting-step heuristic
+        (kin_order_states: key, min/max, histogram, scan and scatter kernels)
+        and integrates in that order.  Capture itself runs nothing.
         """
         import torch
+        if order_by not in (None, "heuristic"):
+            raise ValueError(f"order_by: {order_by!r}")
         g = torch.cuda.CUDAGraph()
+        bufs = ()
+        if order_by == "heuristic":
+            n = int(T.shape[0])
+            bufs = (torch.empty(n, dtype=torch.float64, device=T.device),
+                    torch.empty(n, dtype=torch.int32, device=T.device))
         with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            s = torch.cuda.current_stream()
+            if bufs:
+                self.order_states(Y, T, P, rtol, atol, key=bufs[0], order=bufs[1], stream=s)
+                opt["order"] = bufs[1]
             self.integrate(Y, T, P, dt, rtol, atol, status=status, counters=counters,
-                           stream=torch.cuda.current_stream(), **opt)
+                           stream=s, **opt)
+        g.kin_buffers = bufs  # the key and order live as long as the graph
         return g
 
     def integrate_default(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, stream=None):
@@ -264,7 +285,30 @@ class Mechanism:
         secs = secs[~np.isnan(secs)]
         layout = {LAYOUT_PLAIN: "plain", LAYOUT_QUEUE: "queue", LAYOUT_WARP: "warp"}[best.layout]
         return dict(layout=layout, block=best.block, queue_refill=best.queue_refill,
-                    grid_per_sm=best.grid_per_sm), secs.tolist()
+                    grid_per_sm=best.grid_per_sm, lanes=best.lanes), secs.tolist()
+
+    def order_states(self, Y, T, P, rtol=1e-6, atol=1e-10, *, key=None, given_key=None,
+                     order=None, stream=None):
+        """kin_order_states: (order, key) device tensors, order an int32
+        permutation that sorts the key ascending (stiffest first).  With
+        given_key (float64 [n], e.g. the predictor's ln h0) that key is used
+        as is; otherwise the starting-step heuristic's ln h0 is computed into
+        key (a new tensor when key is None).  order: optional output buffer."""
+        import torch
+        if given_key is not None:
+            key, mode = given_key, KEY_GIVEN
+        else:
+            mode = KEY_STEP_HEURISTIC
+        n = int(T.shape[0]) if T is not None else int(key.shape[0])
+        dev = (T if T is not None else key).device
+        if order is None:
+            order = torch.empty(n, dtype=torch.int32, device=dev)
+        if key is None:
+            key = torch.empty(n, dtype=torch.float64, device=dev)
+        _check(lib().kin_order_states(self.handle, _ptr(Y), _ptr(T), _ptr(P), n, float(rtol),
+                                      float(atol), mode, _ptr(key), _ptr(order),
+                                      _stream(stream)), "kin_order_states")
+        return order, key
 
     def stats(self):
         """Totals of the last integration (kin_get_stats)."""

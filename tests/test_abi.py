@@ -95,3 +95,11 @@ def test_integrate_rejects_bad_arguments():
     assert L.kin_get_stats(None, p) == kin.KIN_ERR_INVALID_ARG
     assert L.kin_radau_constants(p, 5) == kin.KIN_ERR_INVALID_ARG
     assert kin.lib().kin_status_string(kin.KIN_ERR_MECH) == b"invalid mechanism description"
+
+
+def test_order_states_validates_on_host():
+    L = kin.lib()
+    assert L.kin_order_states(None, None, None, None, 4, 1e-6, 1e-10, 1, None, None,
+                              None) == kin.KIN_ERR_INVALID_ARG
+    o = kin.options()
+    assert o.order is None

@@ -307,6 +307,92 @@ def test_graph_capture_replays_the_integration(h2):
         np.testing.assert_array_equal(Y.cpu().numpy(), Yd)
         np.testing.assert_array_equal(T.cpu().numpy(), Td)
     assert mg.stats()["naccpt"] > 0
+    # the ordered form: ordering kernels + integration in one graph, same bits
+    g2 = mg.capture(Y, T, P, 1e-5, layout="plain", lu_fp32=True, order_by="heuristic")
+    Y.copy_(Y0)
+    T.copy_(T0)
+    g2.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Y.cpu().numpy(), Yd)
+    np.testing.assert_array_equal(T.cpu().numpy(), Td)
+    o = g2.kin_buffers[1].cpu().numpy()
+    np.testing.assert_array_equal(np.sort(o), np.arange(st.n))
+
+
+def test_order_states_sorts_by_the_step_heuristic(h2):
+    """kin_order_states: a permutation sorting the starting-step heuristic's
+    ln h0 ascending (to the bin width); the key matches the heuristic computed
+    from the oracle's right-hand side."""
+    mech, mg, st = h2
+    n = st.n
+    Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
+    order, key = mg.order_states(Y, T, P, 1e-6, 1e-10)
+    torch.cuda.synchronize()
+    o, k = order.cpu().numpy(), key.cpu().numpy()
+    np.testing.assert_array_equal(np.sort(o), np.arange(n))
+    width = (k.max() - k.min()) / 4096
+    assert np.all(np.diff(k[o]) >= -width * (1 + 1e-9))
+    om = O.OracleMech(mech)
+    y = O.state_vector(st)
+    r = 0.1 * 1e-6 ** (2.0 / 3.0)
+    a = r * 1e-10 / 1e-6
+    for i in range(0, n, 97):
+        f = O.rhs(om, st.P[i], y[:, i])[0]
+        sc = a + r * np.abs(y[:, i])
+        d0 = np.sqrt(np.mean((y[:, i] / sc) ** 2))
+        d1 = np.sqrt(np.mean((f / sc) ** 2))
+        h0 = 1e-6 if (d0 < 1e-5 or d1 < 1e-5) else 0.01 * d0 / d1
+        np.testing.assert_allclose(k[i], np.log(h0), rtol=1e-9, atol=1e-9)
+    # a given key: the reverse order (to the bin width)
+    o2, _ = mg.order_states(None, None, None, given_key=-key)
+    o2 = o2.cpu().numpy()
+    np.testing.assert_array_equal(np.sort(o2), np.arange(n))
+    assert np.all(np.diff(-k[o2]) >= -width * (1 + 1e-9))
+
+
+def test_ordered_integration_gives_the_same_bits(h2):
+    """The slot that carries a state does not change its result."""
+    mech, mg, st = h2
+    Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
+    order, _ = mg.order_states(Y, T, P)
+    for layout, lanes in (("plain", 0), ("queue", 0), ("warp", 32), ("warp", 8)):
+        a = run_gpu(mg, st, 1e-5, layout=layout, lu_fp32=True, lanes=lanes)
+        b = run_gpu(mg, st, 1e-5, layout=layout, lu_fp32=True, order=order, lanes=lanes)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_order_entries_out_of_range_are_skipped_and_reported(h2):
+    mech, mg, st = h2
+    sub = st.subset(np.arange(64))
+    order = torch.arange(64, dtype=torch.int32, device="cuda")
+    order[5] = 64 + 7
+    order[9] = -3
+    Y, T, P = dev(sub.Y), dev(sub.T), dev(sub.P)
+    mg.integrate(Y, T, P, 1e-5, layout="plain", order=order)
+    torch.cuda.synchronize()
+    with pytest.raises(kin.KinError):
+        mg.stats()
+    Tg = T.cpu().numpy()
+    assert Tg[5] == sub.T[5] and Tg[9] == sub.T[9]   # never integrated
+    assert np.sum(Tg != sub.T) >= 50
+
+
+def test_state_whose_last_step_is_below_round_off_finishes(ch4):
+    """A CH4 state of the 2^16-state workload whose controller leaves a final
+    remainder below the round-off of t at dt = 1e-4: it finishes (status 0) on
+    both sides, and the FP64 result matches the oracle."""
+    mech, mg, _ = ch4
+    _, st, _ = synth.workload("ch4_2p16")
+    sub = st.subset(np.array([2410]))
+    Yo, To, co = O.integrate(mech, sub, 1e-4)
+    assert co[0, 7] == 0
+    for layout, f32 in (("warp", False), ("warp", True), ("plain", False)):
+        Yg, Tg, cg, sg = run_gpu(mg, sub, 1e-4, layout=layout, lu_fp32=f32)
+        assert sg[0] == 0, (layout, f32, cg)
+        if not f32:
+            eT, eY, _ = parity(Yg, Tg, Yo, To)
+            assert eT <= RTOL_PARITY and eY <= RTOL_PARITY
 
 
 def test_edge_sizes_and_ragged_tail(h2):
@@ -440,7 +526,8 @@ def test_autotuner_returns_a_valid_choice_and_keeps_inputs(h2):
     best, secs = mg.autotune(Y, T, P, 1e-5, lu_fp32=True)
     assert best["layout"] in ("plain", "queue", "warp")
     assert best["layout"] == "warp" or best["block"] in (32, 64)
-    assert len(secs) == 9 and all(s > 0 for s in secs)
+    assert best["layout"] != "warp" or best["lanes"] in (4, 8, 16, 32)
+    assert len(secs) == 12 and all(s > 0 for s in secs)
     np.testing.assert_array_equal(Y.cpu().numpy(), st.Y)
     np.testing.assert_array_equal(T.cpu().numpy(), st.T)
     a = run_gpu(mg, st, 1e-5, lu_fp32=True, **{k: v for k, v in best.items() if k != "grid_per_sm"})
@@ -465,11 +552,12 @@ def test_autotuner_large_mechanism_returns_warp_untimed(ch4):
 # WARP layout (one state per warp)
 # ----------------------------------------------------------------------------
 
+@pytest.mark.parametrize("lanes", [32, 16, 8, 4])
 @pytest.mark.parametrize("lu_fp32", [False, True])
-def test_warp_layout_h2_parity(h2, h2_oracle, lu_fp32):
+def test_warp_layout_h2_parity(h2, h2_oracle, lu_fp32, lanes):
     mech, mg, st = h2
     Yo, To, co = h2_oracle
-    Yg, Tg, cg, sg = run_gpu(mg, st, 1e-6, layout="warp", lu_fp32=lu_fp32)
+    Yg, Tg, cg, sg = run_gpu(mg, st, 1e-6, layout="warp", lu_fp32=lu_fp32, lanes=lanes)
     assert np.all(sg == 0)
     eT, eY, per = parity(Yg, Tg, Yo, To)
     if not lu_fp32:
@@ -492,6 +580,37 @@ def test_warp_layout_ch4_parity(ch4):
     assert np.all(sf == 0)
     E = O.error_norm(np.concatenate([Tf[None], Yf[:-1]]), np.concatenate([To[None], Yo[:-1]]))
     assert np.median(E) < 1.0 and E.max() < 50.0, (np.median(E), E.max())
+
+
+@pytest.mark.parametrize("lanes", [16, 8, 4])
+def test_lane_groups_fd_jacobian_edge_sizes_and_dt(h2, lanes):
+    """Groups of 4, 8 and 16 lanes: FD Jacobian, ragged counts (groups of one
+    warp that end at different times), dt = 1e-4 against the 32-lane form."""
+    mech, mg, st = h2
+    for n in (1, 3, 9, 70):
+        sub = st.subset(np.arange(n))
+        Yo, To, co = O.integrate(mech, sub, 1e-6, jac_kind=1)
+        Yg, Tg, cg, sg = run_gpu(mg, sub, 1e-6, layout="warp", jac_fd=True, lanes=lanes)
+        assert np.all(sg == 0)
+        E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), np.concatenate([To[None], Yo[:-1]]))
+        assert E.max() < 1.0, E.max()
+    sub = st.subset(np.arange(256))
+    a = run_gpu(mg, sub, 1e-4, layout="warp", lanes=32)
+    b = run_gpu(mg, sub, 1e-4, layout="warp", lanes=lanes)
+    assert np.all(a[3] == 0) and np.all(b[3] == 0)
+    E = O.error_norm(np.concatenate([b[1][None], b[0][:-1]]), np.concatenate([a[1][None], a[0][:-1]]))
+    assert np.median(E) < 1.0 and E.max() < 50.0, (np.median(E), E.max())
+
+
+def test_lane_groups_reject_large_mechanisms_and_bad_counts(h2, ch4):
+    mech, mg, st = ch4
+    sub = st.subset(np.arange(4))
+    with pytest.raises(kin.KinError):
+        run_gpu(mg, sub, 1e-6, layout="warp", lanes=8)     # 53 species > 15
+    mech, mg, st = h2
+    sub = st.subset(np.arange(4))
+    with pytest.raises(kin.KinError):
+        run_gpu(mg, sub, 1e-6, layout="warp", lanes=12)
 
 
 def test_warp_layout_fd_jacobian_and_edge_sizes(ch4):

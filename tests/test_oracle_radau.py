@@ -161,3 +161,24 @@ def test_max_steps_status_keeps_last_accepted_state():
                     max_steps=3)
     assert st["status"] == 1 and st["naccpt"] <= 3
     assert np.all(np.isfinite(y))
+
+
+def test_final_step_below_round_off_of_t_ends_the_integration():
+    """Reading of the fixed global step (Sec. 2.3): a last step shorter than
+    the round-off of t means the state is already at t1, so the integration
+    ends there (status 0, the state unchanged) instead of reporting a step
+    size underflow.  A step that short anywhere else is still an underflow."""
+    lam = -1.0
+    y, st = O.radau(lambda t, v: lam * v, lambda t, v: np.array([[lam]]), [1.0],
+                    1.0, 1.0 + 4e-16)
+    assert st["status"] == 0 and st["nstep"] == 1 and st["naccpt"] == 0
+    assert y[0] == 1.0
+    # a remainder of a few ulps of t still takes an ordinary step
+    y, st = O.radau(lambda t, v: lam * v, lambda t, v: np.array([[lam]]), [1.0],
+                    1.0, 1.0 + 1e-13)
+    assert st["status"] == 0 and st["naccpt"] == 1
+    np.testing.assert_allclose(y[0], np.exp(lam * 1e-13), rtol=1e-15)
+    # a step forced below round-off before the end is an underflow
+    y, st = O.radau(lambda t, v: lam * v, lambda t, v: np.array([[lam]]), [1.0],
+                    1.0, 2.0, h0=1e-18)
+    assert st["status"] == 2
