@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--n", type=int, default=0, help="states (0 = the workload's 2^20)")
     p.add_argument("--no-extras", action="store_true", help="skip the comparison legs")
     p.add_argument("--cpu-sample", type=int, default=2048)
-    p.add_argument("--order", default="none", choices=["none", "heuristic"],
+    p.add_argument("--order", default="heuristic", choices=["none", "heuristic"],
                    help="order the states by the starting-step heuristic inside each step")
     p.add_argument("--graph", type=int, default=1,
                    help="replay the integration as a captured CUDA graph (1) or call it (0)")
@@ -172,7 +172,9 @@ def run_ours(args, rank, world):
         best, secs = mg.autotune(Y0[:, :m].contiguous(), T0[:m].contiguous(), P[:m].contiguous(),
                                  args.dt, RTOL, ATOL, stream=stream, lu_fp32=bool(args.fp32),
                                  jac_fd=args.jac == "fd")
-        tune = {"states": m, "best": best, "candidate_seconds": [round(x, 4) for x in secs]}
+        tune = {"states": m, "best": best, "candidate_seconds": [round(x, 4) for x in secs],
+                "candidates": "plain 64/32, queue 64 refill 1/4/8/16/32, queue 32, "
+                              "warp lanes 32/16/8/4 (-1: skipped)"}
         opt = dict(layout=best["layout"], block=best["block"], queue_refill=best["queue_refill"],
                    lanes=best["lanes"], lu_fp32=bool(args.fp32), jac_fd=args.jac == "fd")
     else:

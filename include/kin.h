@@ -199,8 +199,11 @@ int kin_integrate_host(kin_mech *m, double *Y, double *T, const double *P, int64
  * grouped WARP forms (9).  For ns > 16 the per-thread matrices do not fit
  * on chip and WARP (32 lanes) is returned without timing.  The other option fields (precision,
  * Jacobian, limits; h0/z0 must be NULL) come from base (NULL = defaults).
- * seconds: host [max_candidates] or NULL, each timed candidate's device time
- * in that order (entries past the timed ones are not written).  Allocates
+ * Once a WARP candidate takes over twice the best time so far, the WARP
+ * candidates after it (smaller lane groups) are skipped.
+ * seconds: host [max_candidates] or NULL, each candidate's device time in
+ * that order, -1 for a skipped one (entries past the candidates are not
+ * written).  Allocates
  * and frees temporary device copies of the states.  Synchronises the
  * stream. */
 int kin_autotune(kin_mech *m, const double *Y, const double *T, const double *P, int64_t n,

@@ -32,6 +32,8 @@ struct kin_mech {
   unsigned long long *d_totals = nullptr;  // [0..6] sums, [7] failed, [8] max steps, [9] queue,
                                            // [10] order entries out of range
   void *d_order_ws = nullptr;              // kin_order_states workspace
+  void *d_gscratch = nullptr;              // WARP layout: per-group Jacobian slots
+  int64_t gslots = 0;
   cudaStream_t last_stream = nullptr;
   // host-call buffers
   double *h_Y = nullptr, *h_T = nullptr, *h_P = nullptr;
@@ -106,6 +108,11 @@ static RadauConst radau_constants_host() {
   rc.d[0] = -(13.0 + 7.0 * s6) / 3.0;
   rc.d[1] = (-13.0 + 7.0 * s6) / 3.0;
   rc.d[2] = -1.0 / 3.0;
+  rc.ic1 = 1.0 / rc.c1;
+  rc.ic2 = 1.0 / rc.c2;
+  rc.ic1m1 = 1.0 / (rc.c1 - 1.0);
+  rc.ic2m1 = 1.0 / (rc.c2 - 1.0);
+  rc.ic1mc2 = 1.0 / (rc.c1 - rc.c2);
   return rc;
 }
 
@@ -275,14 +282,14 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
   L.dTmid = o; o += ns;
   L.dcp = o; o += 2 * ns * NCP;
   L.dh = o; o += 2 * ns * NH;
-  L.ds = o; o += 2 * ns * NS;
+  L.dg = o; o += 2 * ns * NG;
   L.dlnA = o; o += nr;
   L.db = o; o += nr;
   L.dTh = o; o += nr;
   L.dtroe = o; o += NTROE * (ntroe > 0 ? ntroe : 1);
   L.deff = o; o += (neff > 0 ? neff : 1);
   L.dexp = o; o += EXP_TAB;
-  L.nd = o;
+  L.dnu = o; o += nr;
   int q = 0;
   L.islot = q; q += 6 * nr;
   L.imeta = q; q += nr;
@@ -302,6 +309,8 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
   L.icsr0 = q; q += ns + 1;
   L.icsr = q; q += (ncsr > 0 ? ncsr : 1);
   L.ni = q;
+  L.dcsrnu = o; o += (ncsr > 0 ? ncsr : 1);
+  L.nd = o;
   dt.assign(L.nd, 0.0);
   it.assign(L.ni, 0);
   for (int k = 0; k < ns; ++k) {
@@ -313,12 +322,13 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
       const double *a = p + 3 + 7 * r;
       double *cp = &dt[L.dcp + (2 * k + r) * NCP];
       double *h = &dt[L.dh + (2 * k + r) * NH];
-      double *s = &dt[L.ds + (2 * k + r) * NS];
+      double *g = &dt[L.dg + (2 * k + r) * NG];
       for (int j = 0; j < 5; ++j) cp[j] = a[j];
       h[0] = a[0]; h[1] = a[1] / 2.0; h[2] = a[2] / 3.0; h[3] = a[3] / 4.0; h[4] = a[4] / 5.0;
       h[5] = a[5];
-      s[0] = a[0]; s[1] = a[1]; s[2] = a[2] / 2.0; s[3] = a[3] / 3.0; s[4] = a[4] / 4.0;
-      s[5] = a[6];
+      // g = s/R - h/RT: a0 (ln T - 1) + a1 T/2 + a2 T^2/6 + a3 T^3/12 + a4 T^4/20 + a6 - a5/T
+      g[0] = a[0]; g[1] = a[1] / 2.0; g[2] = a[2] / 6.0; g[3] = a[3] / 12.0;
+      g[4] = a[4] / 20.0; g[5] = a[6] - a[0]; g[6] = -a[5];
     }
   }
   // 2^(j/128), rounded to double, for the table-driven exponential
@@ -362,12 +372,16 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
       troe_idx = tr++;
     }
     it[L.imeta + i] = t | (nre << 2) | (npr << 4) | (ne << 8) | (troe_idx << 16);
+    dt[L.dnu + i] = (double)(npr - nre);
   }
   {
     int c = 0;
     for (int k = 0; k < ns; ++k) {
       it[L.icsr0 + k] = c;
-      for (int code : sp_list[k]) it[L.icsr + c++] = code;
+      for (int code : sp_list[k]) {
+        dt[L.dcsrnu + c] = (double)((code & 15) - 8);
+        it[L.icsr + c++] = code;
+      }
     }
     it[L.icsr0 + ns] = c;
   }
@@ -387,13 +401,20 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
   KIN_CUDA_TRY(cudaGetDevice(&dev));
   int rc = ensure_constants(dev);
   if (rc) return rc;
+  int sms = 0;
+  KIN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   kin_mech *m = new kin_mech();
   m->device = dev;
   m->L = L;
+  // WARP layout: one Jacobian slot per resident group (up to 64 groups of
+  // 4-16 lanes per SM for ns <= 15, 8 whole warps per SM beyond)
+  m->gslots = (int64_t)sms * (L.ns <= 15 ? 64 : 8);
+  const size_t gbytes = (size_t)m->gslots * L.ns * (L.ns + 1) * sizeof(double);
   if (cudaMalloc(&m->d_tab, sizeof(double) * L.nd) != cudaSuccess ||
       cudaMalloc(&m->d_itab, sizeof(int) * L.ni) != cudaSuccess ||
       cudaMalloc(&m->d_totals, sizeof(unsigned long long) * 16) != cudaSuccess ||
-      cudaMalloc(&m->d_order_ws, order_workspace_bytes()) != cudaSuccess) {
+      cudaMalloc(&m->d_order_ws, order_workspace_bytes()) != cudaSuccess ||
+      cudaMalloc(&m->d_gscratch, gbytes) != cudaSuccess) {
     (void)cudaGetLastError();
     kin_destroy(m);
     return KIN_ERR_NOMEM;
@@ -417,6 +438,7 @@ extern "C" void kin_destroy(kin_mech *m) {
   cudaFree(m->d_itab);
   cudaFree(m->d_totals);
   cudaFree(m->d_order_ws);
+  cudaFree(m->d_gscratch);
   cudaFree(m->h_Y);
   cudaFree(m->h_T);
   cudaFree(m->h_P);
@@ -495,6 +517,8 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   a.rp.stop_after = o.stop_after;
   a.refill_min = o.queue_refill > 0 ? o.queue_refill : 1;
   a.order = o.order;
+  a.gscratch = m->d_gscratch;
+  a.gslots = m->gslots;
   int dev = 0, sms = 0;
   KIN_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != m->device) return KIN_ERR_INVALID_ARG;
@@ -688,8 +712,15 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
     return KIN_ERR_NOMEM;
   }
   // the first candidate runs twice: the first launch also pays one-time costs
+  float prev_group_ms = -1.0f;  // the last WARP candidate's time
   for (int run = -1; run < nc; ++run) {
     const Cand &c = cands[run < 0 ? 0 : run];
+    // smaller lane groups only pay when the larger one came close: stop
+    // timing them once a WARP candidate ran over twice the best time
+    if (run >= 0 && c.layout == KIN_LAYOUT_WARP && prev_group_ms > 2.0f * best_ms) {
+      if (seconds) seconds[run] = -1.0;
+      continue;
+    }
     kin_options o = b;
     o.layout = c.layout;
     o.block = c.block;
@@ -712,6 +743,7 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
       return rc ? rc : KIN_ERR_CUDA;
     }
     if (run < 0) continue;
+    if (c.layout == KIN_LAYOUT_WARP) prev_group_ms = ms;
     if (seconds) seconds[run] = ms * 1e-3;
     if (best_i < 0 || ms < best_ms) {
       best_i = run;

@@ -29,7 +29,7 @@ struct MechLayout {
   int ns, nr, neff;
   int nd, ni;  // table sizes in doubles / ints
   // double-table offsets
-  int dW, dinvW, dTmid, dcp, dh, ds, dlnA, db, dTh, dtroe, deff, dexp;
+  int dW, dinvW, dTmid, dcp, dh, dg, dlnA, db, dTh, dtroe, deff, dexp, dnu, dcsrnu;
   // int-table offsets
   int islot, imeta, ieff0, itroe, ieffsp;
   int icsr0, icsr;  // species -> (reaction, net nu) lists: offsets [ns+1], entries
@@ -38,8 +38,9 @@ struct MechLayout {
 // per-species coefficient blocks (two ranges each):
 //   cp/R = c0 + T(c1 + T(c2 + T(c3 + T c4)))                 (5)
 //   h/RT = c0 + T(c1 + T(c2 + T(c3 + T c4))) + c5 / T        (6)
-//   s/R  = c0 lnT + T(c1 + T(c2 + T(c3 + T c4))) + c5        (6)
-constexpr int NCP = 5, NH = 6, NS = 6;
+//   g    = s/R - h/RT
+//        = c0 lnT + T(c1 + T(c2 + T(c3 + T c4))) + c5 + c6 / T (7)
+constexpr int NCP = 5, NH = 6, NG = 7;
 // Troe block per falloff reaction: k0 lnA, k0 b, k0 Theta, a, 1/T***, 1/T*, T**
 constexpr int NTROE = 7;
 
@@ -53,7 +54,9 @@ __device__ __forceinline__ int meta_troe(int w) { return w >> 16; }
 
 struct MechView {
   int ns, nr;
-  const double *W, *invW, *Tmid, *cp, *h, *s, *lnA, *b, *Th, *troe, *eff, *etab;
+  const double *W, *invW, *Tmid, *cp, *h, *gb, *lnA, *b, *Th, *troe, *eff, *etab;
+  const double *dnu;      // per reaction: sum of product minus reactant coefficients
+  const double *csrnu;    // per species -> reaction entry: the net coefficient nu
   const int *slot, *meta, *eff0, *effsp;
   const int *csr0, *csr;  // entry = reaction << 4 | (nu + 8)
 };
@@ -67,13 +70,15 @@ __device__ __forceinline__ MechView make_view(const MechLayout &L, const double 
   v.Tmid = d + L.dTmid;
   v.cp = d + L.dcp;
   v.h = d + L.dh;
-  v.s = d + L.ds;
+  v.gb = d + L.dg;
   v.lnA = d + L.dlnA;
   v.b = d + L.db;
   v.Th = d + L.dTh;
   v.troe = d + L.dtroe;
   v.eff = d + L.deff;
   v.etab = d + L.dexp;
+  v.dnu = d + L.dnu;
+  v.csrnu = d + L.dcsrnu;
   v.slot = i + L.islot;
   v.meta = i + L.imeta;
   v.eff0 = i + L.ieff0;
@@ -106,8 +111,8 @@ __device__ __forceinline__ double poly_cp(const double *c, double T) {
 __device__ __forceinline__ double poly_h(const double *c, double T, double invT) {
   return c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4]))) + c[5] * invT;
 }
-__device__ __forceinline__ double poly_s(const double *c, double T, double logT) {
-  return c[0] * logT + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4]))) + c[5];
+__device__ __forceinline__ double poly_g(const double *c, double T, double logT, double invT) {
+  return c[0] * logT + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4]))) + c[5] + c[6] * invT;
 }
 // d(cp/R)/dT from the cp coefficients
 __device__ __forceinline__ double poly_dcp(const double *c, double T) {
@@ -247,8 +252,7 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
     const double *cc = m.cp + (2 * k + r) * NCP;
     const double cp = poly_cp(cc, T);
     const double h = poly_h(m.h + (2 * k + r) * NH, T, invT);
-    const double s = poly_s(m.s + (2 * k + r) * NS, T, logT);
-    w.g[k] = s - h;
+    w.g[k] = poly_g(m.gb + (2 * k + r) * NG, T, logT, invT);
     w.hs[k] = h;
     w.cpk[k] = cp;
     cpm += Yk * cp * m.invW[k];
@@ -274,7 +278,7 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
     const int *sl = m.slot + 6 * i;
     const int nre = meta_nreac(meta), npr = meta_nprod(meta), type = meta_type(meta);
     const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
-    double lnKc = (npr - nre) * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
+    double lnKc = m.dnu[i] * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
     for (int s = 0; s < nre; ++s) {
       lnKc -= w.g[sl[s]];
       dH -= w.hs[sl[s]];
@@ -308,7 +312,7 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
     for (int s = 0; s < npr; ++s) w.wd[sl[3 + s]] += q;
     if (wantJ) {
       // d ln Kc / dT = sum nu (h/RT) / T - (sum nu) / T
-      const double dlnkr = dlnkf - (dH - (npr - nre)) * invT;
+      const double dlnkr = dlnkf - (dH - m.dnu[i]) * invT;
       const double u = Rn * dphi_dM;
       const double sig_p = phi * (nre * kf * fwd - npr * kr * rev) + u * (M - Ctot);
       const double dqdT = phi * (kf * dlnkf * fwd - kr * dlnkr * rev) + Rn * dphi_dT -
@@ -442,26 +446,31 @@ __device__ __noinline__ int lu_real(int n, LT *a, int *ip) {
   return 0;
 }
 
-template <typename LT, typename VT>
+// Solve LU x = b in place.  The right-hand side is rounded to the matrix
+// type once, the substitution runs in LT, and the result is widened back.
+template <int MAXN, typename LT, typename VT>
 __device__ __noinline__ void lu_solve_real(int n, const LT *lu, const int *ip, VT *b) {
+  LT v[MAXN];
+  for (int k = 0; k < n; ++k) v[k] = LT(b[k]);
   for (int k = 0; k < n; ++k) {
-    int p = ip[k];
+    const int p = ip[k];
     if (p != k) {
-      VT t = b[k];
-      b[k] = b[p];
-      b[p] = t;
+      const LT t = v[k];
+      v[k] = v[p];
+      v[p] = t;
     }
   }
   for (int i = 1; i < n; ++i) {
-    LT s = LT(b[i]);
-    for (int j = 0; j < i; ++j) s -= lu[i * n + j] * LT(b[j]);
-    b[i] = VT(s);
+    LT s = v[i];
+    for (int j = 0; j < i; ++j) s -= lu[i * n + j] * v[j];
+    v[i] = s;
   }
   for (int i = n - 1; i >= 0; --i) {
-    LT s = LT(b[i]);
-    for (int j = i + 1; j < n; ++j) s -= lu[i * n + j] * LT(b[j]);
-    b[i] = VT(s / lu[i * n + i]);
+    LT s = v[i];
+    for (int j = i + 1; j < n; ++j) s -= lu[i * n + j] * v[j];
+    v[i] = s / lu[i * n + i];
   }
+  for (int k = 0; k < n; ++k) b[k] = VT(v[k]);
 }
 
 // complex (a + ib) / (c + id), Smith's scaling
@@ -518,41 +527,50 @@ __device__ __noinline__ int lu_cplx(int n, LT *ar, LT *ai, int *ip) {
   return 0;
 }
 
-template <typename LT, typename VT>
+template <int MAXN, typename LT, typename VT>
 __device__ __noinline__ void lu_solve_cplx(int n, const LT *lr, const LT *li, const int *ip, VT *br,
-                              VT *bi) {
+                                           VT *bi) {
+  LT vr[MAXN], vi[MAXN];
   for (int k = 0; k < n; ++k) {
-    int p = ip[k];
+    vr[k] = LT(br[k]);
+    vi[k] = LT(bi[k]);
+  }
+  for (int k = 0; k < n; ++k) {
+    const int p = ip[k];
     if (p != k) {
-      VT t = br[k];
-      br[k] = br[p];
-      br[p] = t;
-      t = bi[k];
-      bi[k] = bi[p];
-      bi[p] = t;
+      LT t = vr[k];
+      vr[k] = vr[p];
+      vr[p] = t;
+      t = vi[k];
+      vi[k] = vi[p];
+      vi[p] = t;
     }
   }
   for (int i = 1; i < n; ++i) {
-    LT sr = LT(br[i]), si = LT(bi[i]);
+    LT sr = vr[i], si = vi[i];
     for (int j = 0; j < i; ++j) {
-      LT xr = LT(br[j]), xi = LT(bi[j]);
+      const LT xr = vr[j], xi = vi[j];
       sr -= lr[i * n + j] * xr - li[i * n + j] * xi;
       si -= lr[i * n + j] * xi + li[i * n + j] * xr;
     }
-    br[i] = VT(sr);
-    bi[i] = VT(si);
+    vr[i] = sr;
+    vi[i] = si;
   }
   for (int i = n - 1; i >= 0; --i) {
-    LT sr = LT(br[i]), si = LT(bi[i]);
+    LT sr = vr[i], si = vi[i];
     for (int j = i + 1; j < n; ++j) {
-      LT xr = LT(br[j]), xi = LT(bi[j]);
+      const LT xr = vr[j], xi = vi[j];
       sr -= lr[i * n + j] * xr - li[i * n + j] * xi;
       si -= lr[i * n + j] * xi + li[i * n + j] * xr;
     }
     LT qr, qi;
     cdiv(sr, si, lr[i * n + i], li[i * n + i], qr, qi);
-    br[i] = VT(qr);
-    bi[i] = VT(qi);
+    vr[i] = qr;
+    vi[i] = qi;
+  }
+  for (int k = 0; k < n; ++k) {
+    br[k] = VT(vr[k]);
+    bi[k] = VT(vi[k]);
   }
 }
 

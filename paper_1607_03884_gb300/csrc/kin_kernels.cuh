@@ -34,6 +34,8 @@ struct KernelArgs {
   RadauParams rp;
   int refill_min;        // QUEUE: idle lanes of a warp that trigger a refill
   const int32_t *order;  // slot -> state permutation or null (identity)
+  void *gscratch;        // WARP: per-group Jacobian slots (N x (N+1) doubles each)
+  int64_t gslots;        // number of slots in gscratch
 };
 
 // The state a slot carries: order[slot] when an order is given, else the
@@ -149,16 +151,19 @@ __global__ void __launch_bounds__(64) k_integrate_queue(KernelArgs a) {
 // WARP layout: one state per group of L lanes; groups pop states from the
 // atomic queue.
 template <int L, typename LT, bool FDJ>
-__global__ void __launch_bounds__(128) k_integrate_lanes(KernelArgs a) {
+__global__ void __launch_bounds__(256) k_integrate_lanes(KernelArgs a) {
   using G = Grp<L>;
   constexpr int WR = G::WR;
   extern __shared__ double smem[];
-  const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
+  // the mechanism tables are read through L1 from global memory: shared
+  // memory holds only the groups' matrices and vectors
+  const MechView m = make_view(a.L, a.tab, a.itab);
   const int N = m.ns, lane = G::lane(), grp = (int)(threadIdx.x / L);
   const int64_t n = a.rp.n;
-  char *base = reinterpret_cast<char *>(smem) + (smem_bytes(a.L) + 15) / 16 * 16 +
-               (size_t)grp * warp_buf_bytes(N, m.nr, sizeof(LT), G::CAP);
-  const WarpBuf<LT> b = carve_warp_buf<LT>(base, N, m.nr, G::CAP);
+  char *base = reinterpret_cast<char *>(smem) + (size_t)grp * warp_buf_bytes(N, m.nr, sizeof(LT));
+  const int64_t slot = (int64_t)blockIdx.x * (blockDim.x / L) + grp;  // < gslots (launch)
+  LT *Jg = reinterpret_cast<LT *>(a.gscratch) + slot * (int64_t)N * (N + 1);
+  const WarpBuf<LT> b = carve_warp_buf<LT>(base, N, m.nr, Jg);
   unsigned long long *queue = a.totals + 9;
   WStateT<WR> w;
   StepState s;
@@ -212,20 +217,20 @@ __global__ void __launch_bounds__(128) k_integrate_lanes(KernelArgs a) {
 }
 
 // Shared memory of one block of `warps` warps for L lanes per state.
-__host__ __device__ inline size_t lanes_smem_bytes(const MechLayout &L_, int lanes, int cap,
-                                                   size_t lt, int warps) {
-  return (smem_bytes(L_) + 15) / 16 * 16 +
-         (size_t)warps * (32 / lanes) * warp_buf_bytes(L_.ns, L_.nr, lt, cap);
+__host__ __device__ inline size_t lanes_smem_bytes(const MechLayout &L_, int lanes, size_t lt,
+                                                   int warps) {
+  return (size_t)warps * (32 / lanes) * warp_buf_bytes(L_.ns, L_.nr, lt);
 }
 
 template <int L, typename LT, bool FDJ>
 int launch_lanes(const KernelArgs &a, cudaStream_t st, int sms) {
   using G = Grp<L>;
   if (a.L.ns >= G::CAP) return KIN_ERR_UNSUPPORTED;
+  if (!a.gscratch || a.gslots < 1) return KIN_ERR_UNSUPPORTED;
   const size_t budget = 227 * 1024;
-  int warps = 4;
-  while (warps > 1 && lanes_smem_bytes(a.L, L, G::CAP, sizeof(LT), warps) > budget) --warps;
-  const size_t sm = lanes_smem_bytes(a.L, L, G::CAP, sizeof(LT), warps);
+  int warps = 8;
+  while (warps > 1 && lanes_smem_bytes(a.L, L, sizeof(LT), warps) > budget) --warps;
+  const size_t sm = lanes_smem_bytes(a.L, L, sizeof(LT), warps);
   if (sm > budget) return KIN_ERR_UNSUPPORTED;
   auto kern = k_integrate_lanes<L, LT, FDJ>;
   KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -236,6 +241,8 @@ int launch_lanes(const KernelArgs &a, cudaStream_t st, int sms) {
   const int64_t per_block = (int64_t)warps * (32 / L);
   const int64_t need = (a.rp.n + per_block - 1) / per_block;
   if (grid > need) grid = need;
+  if (grid * per_block > a.gslots) grid = a.gslots / per_block;  // one J slot per group
+  if (grid < 1) return KIN_ERR_UNSUPPORTED;
   kern<<<(unsigned)grid, 32 * warps, sm, st>>>(a);
   KIN_CUDA_TRY(cudaGetLastError());
   return KIN_OK;

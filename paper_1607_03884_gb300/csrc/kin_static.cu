@@ -108,5 +108,7 @@ extern "C" int kin_integrate_static(const kin_mech_desc *desc, double *Y, double
   a.rp.stop_after = 0;
   a.refill_min = 1;
   a.order = nullptr;
+  a.gscratch = nullptr;  // the default (QUEUE) layout needs no group slots
+  a.gslots = 0;
   return launch_dispatch(a, o, st, sms);
 }

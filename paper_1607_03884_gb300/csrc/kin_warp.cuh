@@ -84,60 +84,80 @@ __device__ __forceinline__ double elem(const WVecT<Grp<L>::WR> &x, int g) {
   return Grp<L>::bcast(slot_get<Grp<L>::WR>(x, g / L), g % L);
 }
 
-// Per-group shared-memory slice (N < CAP, nr reactions).
+// Per-group workspace.  E1, E2 and the vectors live in the group's slice of
+// shared memory; the stored Jacobian J (read only to rebuild E1/E2 and for
+// the refinement residual) lives in a per-group slot of a global scratch
+// buffer, which stays in L2.  The FP64 assembly matrix Jd borrows the E2 area
+// (one FP64 N x ld matrix fits in E2r + E2i in either precision): E2 is always
+// refactorised after a new Jacobian.
 template <typename LT>
 struct WarpBuf {
   int ld;
-  LT *J, *E1, *E2r, *E2i;
-  double *Jd;  // FP64 assembly matrix: J itself (FP64) or the E2 area (FP32, rebuilt after)
+  LT *J;  // global, N x ld
+  LT *E1, *E2r, *E2i;
+  double *Jd;
   double *C, *g, *hs, *cpk, *wd, *q;
   double *A, *B, *Tc, *mj, *rW, *Cj;
   LT *v1, *v2;
   int *ip1, *ip2;
 };
 
-__host__ __device__ inline size_t warp_buf_bytes(int N, int nr, size_t lt, int cap) {
-  const size_t ld = (size_t)N + 1;
-  size_t b = (11 * (size_t)cap + (size_t)nr) * sizeof(double);  // C g hs cpk wd A B Tc mj rW Cj, q
-  b += 4 * (size_t)N * ld * lt;                                  // J E1 E2r E2i
-  b += 2 * (size_t)cap * lt;                                     // v1 v2
-  b += 2 * (size_t)cap * sizeof(int);                            // ip1 ip2
+// length of the per-species vectors: N rounded up to even (keeps 8-byte
+// alignment of the float matrices that follow)
+__host__ __device__ inline int warp_nv(int N) { return (N + 1) & ~1; }
+
+// E1's area: the matrix, or the six assembly vectors when those are larger
+// (small N in FP32); a multiple of 8 bytes
+__host__ __device__ inline size_t warp_e1_bytes(int N, size_t lt) {
+  const size_t m = (size_t)N * (N + 1) * lt, v = 6 * (size_t)warp_nv(N) * sizeof(double);
+  return ((m > v ? m : v) + 7) / 8 * 8;
+}
+
+__host__ __device__ inline size_t warp_buf_bytes(int N, int nr, size_t lt) {
+  const size_t ld = (size_t)N + 1, nv = (size_t)warp_nv(N);
+  size_t b = (5 * nv + (size_t)nr) * sizeof(double);  // C g hs cpk wd, q
+  b += warp_e1_bytes(N, lt);                           // E1 (A B Tc mj rW Cj)
+  b += 2 * (size_t)N * ld * lt;                        // E2r E2i
+  b += 2 * nv * lt;                                     // v1 v2
+  b += 2 * nv * sizeof(int);                            // ip1 ip2
   return (b + 15) / 16 * 16;
 }
 
 template <typename LT>
-__device__ WarpBuf<LT> carve_warp_buf(char *p, int N, int nr, int cap) {
+__device__ WarpBuf<LT> carve_warp_buf(char *p, int N, int nr, LT *Jglobal) {
   WarpBuf<LT> w;
   w.ld = N + 1;
+  const int nv = warp_nv(N);
   double *d = reinterpret_cast<double *>(p);
   w.C = d;
-  w.g = d + cap;
-  w.hs = d + 2 * cap;
-  w.cpk = d + 3 * cap;
-  w.wd = d + 4 * cap;
-  w.A = d + 5 * cap;
-  w.B = d + 6 * cap;
-  w.Tc = d + 7 * cap;
-  w.mj = d + 8 * cap;
-  w.rW = d + 9 * cap;
-  w.Cj = d + 10 * cap;
-  w.q = d + 11 * cap;
-  LT *l = reinterpret_cast<LT *>(d + 11 * cap + nr);
-  const int mat = N * w.ld;
-  w.J = l;
-  w.E1 = l + mat;
-  w.E2r = l + 2 * mat;
-  w.E2i = l + 3 * mat;
-  // E2r and E2i are contiguous; in FP32 they hold exactly one FP64 N x ld
-  // matrix (their start is 8-byte aligned: 2 mat floats after a double)
-  w.Jd = sizeof(LT) == sizeof(double) ? reinterpret_cast<double *>(w.J)
-                                      : reinterpret_cast<double *>(w.E2r);
-  l += 4 * mat;
-  w.v1 = l;
-  w.v2 = l + cap;
-  int *ip = reinterpret_cast<int *>(l + 2 * cap);
+  w.g = d + nv;
+  w.hs = d + 2 * nv;
+  w.cpk = d + 3 * nv;
+  w.wd = d + 4 * nv;
+  w.q = d + 5 * nv;
+  char *l = reinterpret_cast<char *>(d + 5 * nv + nr);
+  const int mat = N * w.ld;  // even, so every matrix starts 8-byte aligned
+  w.J = Jglobal;
+  w.E1 = reinterpret_cast<LT *>(l);
+  l += warp_e1_bytes(N, sizeof(LT));
+  w.E2r = reinterpret_cast<LT *>(l);
+  w.E2i = w.E2r + mat;
+  w.Jd = reinterpret_cast<double *>(w.E2r);
+  // the Jacobian assembly's vectors live in the E1 area (sized for both):
+  // like E2, E1 is always refactorised after a new Jacobian
+  double *e1 = reinterpret_cast<double *>(w.E1);
+  w.A = e1;
+  w.B = e1 + nv;
+  w.Tc = e1 + 2 * nv;
+  w.mj = e1 + 3 * nv;
+  w.rW = e1 + 4 * nv;
+  w.Cj = e1 + 5 * nv;
+  LT *v = w.E2r + 2 * mat;
+  w.v1 = v;
+  w.v2 = v + nv;
+  int *ip = reinterpret_cast<int *>(v + 2 * nv);
   w.ip1 = ip;
-  w.ip2 = ip + cap;
+  w.ip2 = ip + nv;
   return w;
 }
 
@@ -180,9 +200,8 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
       const double *cc = m.cp + (2 * k + rg) * NCP;
       const double cp = poly_cp(cc, T);
       const double h = poly_h(m.h + (2 * k + rg) * NH, T, invT);
-      const double s = poly_s(m.s + (2 * k + rg) * NS, T, logT);
       b.C[k] = C;
-      b.g[k] = s - h;
+      b.g[k] = poly_g(m.gb + (2 * k + rg) * NG, T, logT, invT);
       b.hs[k] = h;
       b.cpk[k] = cp;
       cpl += Yk * cp * m.invW[k];
@@ -212,7 +231,7 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
     const int *sl = m.slot + 6 * i;
     const int nre = meta_nreac(meta), npr = meta_nprod(meta), type = meta_type(meta);
     const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
-    double lnKc = (npr - nre) * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
+    double lnKc = m.dnu[i] * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
     for (int s = 0; s < nre; ++s) {
       lnKc -= b.g[sl[s]];
       dH -= b.hs[sl[s]];
@@ -243,7 +262,7 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
     const double Rn = kf * fwd - kr * rev;
     b.q[i] = phi * Rn;
     if (wantJ) {
-      const double dlnkr = dlnkf - (dH - (npr - nre)) * invT;
+      const double dlnkr = dlnkf - (dH - m.dnu[i]) * invT;
       const double u = Rn * dphi_dM;
       const double sig_p = phi * (nre * kf * fwd - npr * kr * rev) + u * (M - Ctot);
       const double dqdT = phi * (kf * dlnkf * fwd - kr * dlnkr * rev) + Rn * dphi_dT -
@@ -291,10 +310,7 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
     const int g = lane + L * r, k = g - 1;
     if (g >= 1 && g < N) {
       double w = 0.0;
-      for (int e = m.csr0[k]; e < m.csr0[k + 1]; ++e) {
-        const int code = m.csr[e];
-        w += (double)((code & 15) - 8) * b.q[code >> 4];
-      }
+      for (int e = m.csr0[k]; e < m.csr0[k + 1]; ++e) w += m.csrnu[e] * b.q[m.csr[e] >> 4];
       b.wd[k] = w;
       f.v[r] = m.W[k] * w * irho;
       ok &= isfinite(f.v[r]);
@@ -368,7 +384,7 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
     const int q = (e / N) * ld + e % N;
     const double v = b.Jd[q];
     okJ &= isfinite(v);
-    if (sizeof(LT) != sizeof(double)) b.J[q] = LT(v);  // one rounding per entry
+    b.J[q] = LT(v);  // one rounding per entry (none in FP64)
   }
   G::sync();
   return G::all(ok && okJ) ? 0 : 4;
@@ -626,8 +642,8 @@ __device__ __noinline__ void warp_solve_cplx(int N, int ld, const LT *lr, const 
 // ---------------------------------------------------------------------------
 template <int WR>
 struct WStateT {
-  WVecT<WR> y, f0, scal, z1, z2, z3, w1, w2, w3, a1, a2, a3, F1, F2, fu, u, fe;
-};
+  WVecT<WR> y, f0, scal, isc, z1, z2, z3, w1, w2, w3, a1, a2, a3, F1, F2, fu, u, fe;
+};  // isc = 1 / scal
 
 template <int L>
 __device__ __forceinline__ double wrms_w(int N, const WVecT<Grp<L>::WR> &v,
@@ -694,6 +710,24 @@ __device__ void warp_start_values(int N, WStateT<Grp<L>::WR> &w, const StepState
   }
 }
 
+// the same norm with reciprocal weights (no division per element)
+template <int L>
+__device__ __forceinline__ double wrms_wi(int N, const WVecT<Grp<L>::WR> &v,
+                                          const WVecT<Grp<L>::WR> &isc) {
+  using G = Grp<L>;
+  const int lane = G::lane();
+  double s = 0.0;
+#pragma unroll
+  for (int r = 0; r < G::WR; ++r) {
+    const int g = lane + L * r;
+    if (g < N) {
+      const double q = v.v[r] * isc.v[r];
+      s += q * q;
+    }
+  }
+  return sqrt(G::sum(s) / N);
+}
+
 // E1 solve for the error estimate, with one FP64-residual refinement when
 // the factorisation is FP32 (as solve_e1_refined).
 template <int L, typename LT>
@@ -745,7 +779,10 @@ __device__ bool warp_init(const MechView &m, const WarpBuf<LT> &b, double P,
     s.need = NEED_LU;
   }
 #pragma unroll
-  for (int r = 0; r < WR; ++r) w.scal.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
+  for (int r = 0; r < WR; ++r) {
+    w.scal.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
+    w.isc.v[r] = 1.0 / w.scal.v[r];
+  }
   if (p.h0) {
     s.h = p.h0[idx];
   } else {
@@ -892,8 +929,8 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
     for (int r = 0; r < WR; ++r) {
       const int g = lane + L * r;
       if (g < N) {
-        const double q1 = w.z1.v[r] / w.scal.v[r], q2 = w.z2.v[r] / w.scal.v[r],
-                     q3 = w.z3.v[r] / w.scal.v[r];
+        const double is = w.isc.v[r];
+        const double q1 = w.z1.v[r] * is, q2 = w.z2.v[r] * is, q3 = w.z3.v[r] * is;
         sum += q1 * q1 + q2 * q2 + q3 * q3;
       }
     }
@@ -927,13 +964,14 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
     return false;
   }
   // error estimate
+  const double ih = 1.0 / s.h;
 #pragma unroll
   for (int r = 0; r < WR; ++r) {
-    w.fe.v[r] = (RC.d[0] * w.z1.v[r] + RC.d[1] * w.z2.v[r] + RC.d[2] * w.z3.v[r]) / s.h;
+    w.fe.v[r] = (RC.d[0] * w.z1.v[r] + RC.d[1] * w.z2.v[r] + RC.d[2] * w.z3.v[r]) * ih;
     w.u.v[r] = w.fe.v[r] + w.f0.v[r];
   }
   warp_solve_e1<L, LT>(N, b, s.h, w.u);
-  double err = fmax(wrms_w<L>(N, w.u, w.scal), 1e-10);
+  double err = fmax(wrms_wi<L>(N, w.u, w.isc), 1e-10);
   if (err >= 1.0 && (s.first || s.reject)) {
 #pragma unroll
     for (int r = 0; r < WR; ++r) w.F2.v[r] = w.y.v[r] + w.u.v[r];
@@ -945,7 +983,7 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
 #pragma unroll
       for (int r = 0; r < WR; ++r) w.u.v[r] = w.fu.v[r] + w.fe.v[r];
       warp_solve_e1<L, LT>(N, b, s.h, w.u);
-      err = fmax(wrms_w<L>(N, w.u, w.scal), 1e-10);
+      err = fmax(wrms_wi<L>(N, w.u, w.isc), 1e-10);
     }
   }
   double hnew;
@@ -963,19 +1001,17 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
         }
       }
   }
-  {
-    const double c1 = RC.c1, c2 = RC.c2;
 #pragma unroll
-    for (int r = 0; r < WR; ++r) {
-      const double z1 = w.z1.v[r], z2 = w.z2.v[r], z3 = w.z3.v[r];
-      w.y.v[r] += z3;
-      w.a1.v[r] = (z2 - z3) / (c2 - 1.0);
-      const double ak = (z1 - z2) / (c1 - c2);
-      const double acont3 = (ak - z1 / c1) / c2;
-      w.a2.v[r] = (ak - w.a1.v[r]) / (c1 - 1.0);
-      w.a3.v[r] = w.a2.v[r] - acont3;
-      w.scal.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
-    }
+  for (int r = 0; r < WR; ++r) {
+    const double z1 = w.z1.v[r], z2 = w.z2.v[r], z3 = w.z3.v[r];
+    w.y.v[r] += z3;
+    w.a1.v[r] = (z2 - z3) * RC.ic2m1;
+    const double ak = (z1 - z2) * RC.ic1mc2;
+    const double acont3 = (ak - z1 * RC.ic1) * RC.ic2;
+    w.a2.v[r] = (ak - w.a1.v[r]) * RC.ic1m1;
+    w.a3.v[r] = w.a2.v[r] - acont3;
+    w.scal.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
+    w.isc.v[r] = 1.0 / w.scal.v[r];
   }
   if (s.last || (p.stop_after > 0 && s.naccpt >= p.stop_after)) return true;
   const bool wantJ = !FDJ && s.theta > THET;

@@ -29,6 +29,13 @@ class Predictor:
     norm: dict          # device float tensors in_mean, in_std, out_mean, out_std
     ns: int
 
+    def scaled(self, factor):
+        """The same network with its first-step prediction multiplied by
+        factor (a shift of the ln h0 output's mean; no extra kernel)."""
+        norm = {k: v.clone() for k, v in self.norm.items()}
+        norm["out_mean"][0:1] += float(np.log(factor))
+        return Predictor(net=self.net, norm=norm, ns=self.ns)
+
     def predict(self, Y, T, P, dt, stream=None):
         import torch
         n = int(T.shape[0])
