@@ -261,7 +261,8 @@ def run_ours(args, rank, world):
         Ph = torch.from_numpy(st.P.copy()).pin_memory()
         Yp = Yh.clone().pin_memory()
         Tp = Th.clone().pin_memory()
-        mg.integrate_host(Yp, Tp, Ph, args.dt, RTOL, ATOL, stream=stream, **opt)
+        hopt = dict(opt, order_by=None if args.order == "none" else args.order)
+        mg.integrate_host(Yp, Tp, Ph, args.dt, RTOL, ATOL, stream=stream, **hopt)
         te = []
         for _ in range(max(1, min(args.steps, 3))):
             Yp.copy_(Yh)
@@ -269,7 +270,7 @@ def run_ours(args, rank, world):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            mg.integrate_host(Yp, Tp, Ph, args.dt, RTOL, ATOL, stream=stream, **opt)
+            mg.integrate_host(Yp, Tp, Ph, args.dt, RTOL, ATOL, stream=stream, **hopt)
             te.append(time.perf_counter() - t0)
         out["e2e"] = {"value": n / float(np.mean(te)), "unit": "states/s",
                       "h2d_bytes_per_step": int(n * (mech.ns + 2) * 8),

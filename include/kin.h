@@ -56,7 +56,8 @@ enum {
   KIN_STATE_MAX_STEPS = 1,   /* internal step limit reached */
   KIN_STATE_H_UNDERFLOW = 2, /* internal step below round-off of t */
   KIN_STATE_SINGULAR = 3,    /* iteration matrix singular 5 times in a row */
-  KIN_STATE_NONFINITE = 4    /* non-finite right-hand side or Jacobian */
+  KIN_STATE_NONFINITE = 4,   /* non-finite right-hand side or Jacobian */
+  KIN_STATE_NEWTON_FIXED = 5 /* kin_options.h_fixed: Newton failed at the fixed step */
 };
 
 /* maximum number of species (N = ns unknowns per state) */
@@ -140,6 +141,20 @@ typedef struct {
   int32_t lanes;         /* KIN_LAYOUT_WARP: lanes per state, 4, 8, 16 or 32
                             (0 = 32).  4, 8 and 16 hold at most 15 species
                             and place 32/lanes states in each warp      (0) */
+  double h_fixed;        /* > 0: constant internal step h_fixed (the last step
+                            clipped onto dt; x + 1.0001 h >= dt ends it),
+                            every step accepted, a fresh Jacobian every step,
+                            Newton iterated until it converges, diverges or
+                            reaches nit (no slow-contraction exit); the error
+                            estimate is still computed.  For
+                            convergence studies (Sec. 2.3).  PLAIN and QUEUE
+                            layouts only; a Newton failure ends the state
+                            with KIN_STATE_NEWTON_FIXED                 (0) */
+  int32_t order_by;      /* kin_integrate_host only: 1 = order the states by
+                            the starting-step heuristic (kin_order_states) in
+                            the entry's own device buffers before integrating;
+                            0 = none.  kin_integrate_ex takes an explicit
+                            order instead and rejects a nonzero value    (0) */
 } kin_options;
 
 /* Per-state counters written by kin_integrate_ex when counters != NULL:

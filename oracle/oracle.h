@@ -70,6 +70,7 @@ typedef struct {
 #define ORC_H_UNDERFLOW 2
 #define ORC_SINGULAR 3
 #define ORC_NONFINITE 4
+#define ORC_NEWTON_FIXED 5 /* Newton failed at a fixed step: no smaller step to retry */
 
 typedef int (*orc_rhs_fn)(void *ctx, double t, const double *y, double *f);
 typedef int (*orc_jac_fn)(void *ctx, double t, const double *y, const double *f0,

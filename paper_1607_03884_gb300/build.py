@@ -21,6 +21,9 @@ LIB = os.path.join(HERE, "libkin.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# optional extra -D definitions (tuning knobs such as KIN_THREAD_MIN_BLOCKS);
+# a change needs build(force=True)
+NVCC_FLAGS += [f for f in os.environ.get("KIN_NVCC_DEFINES", "").split() if f.startswith("-D")]
 
 
 def nvcc() -> str:

@@ -38,6 +38,8 @@ struct kin_mech {
   // host-call buffers
   double *h_Y = nullptr, *h_T = nullptr, *h_P = nullptr;
   int32_t *h_status = nullptr, *h_cnt = nullptr;
+  double *h_key = nullptr;    // host entry: ordering key and permutation
+  int32_t *h_order = nullptr;
   int64_t h_cap = 0;
 };
 
@@ -205,6 +207,8 @@ extern "C" int kin_options_default(kin_options *o) {
   o->stop_after = 0;
   o->order = nullptr;
   o->lanes = 0;
+  o->h_fixed = 0.0;
+  o->order_by = 0;
   return KIN_OK;
 }
 
@@ -443,6 +447,8 @@ extern "C" void kin_destroy(kin_mech *m) {
   cudaFree(m->h_T);
   cudaFree(m->h_P);
   cudaFree(m->h_status);
+  cudaFree(m->h_key);
+  cudaFree(m->h_order);
   cudaFree(m->h_cnt);
   delete m;
 }
@@ -481,8 +487,11 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   if (o.nit < 1 || o.nit > 50 || o.max_steps < 1) return KIN_ERR_INVALID_ARG;
   if (o.queue_refill < 0 || o.queue_refill > 32 || o.stop_after < 0) return KIN_ERR_INVALID_ARG;
   if (o.order && n > INT32_MAX) return KIN_ERR_INVALID_ARG;
+  if (o.order_by != 0) return KIN_ERR_INVALID_ARG;  // host entry only (kin_order_states here)
   if (o.lanes != 0 && o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32)
     return KIN_ERR_INVALID_ARG;
+  if (!(o.h_fixed >= 0.0) || !std::isfinite(o.h_fixed)) return KIN_ERR_INVALID_ARG;
+  if (o.h_fixed > 0.0 && o.layout == KIN_LAYOUT_WARP) return KIN_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   m->last_stream = st;
   KIN_CUDA_TRY(cudaMemsetAsync(m->d_totals, 0, sizeof(unsigned long long) * 16, st));
@@ -515,6 +524,7 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   a.rp.h_first = o.h_first;
   a.rp.z_first = o.z_first;
   a.rp.stop_after = o.stop_after;
+  a.rp.hfixed = o.h_fixed;
   a.refill_min = o.queue_refill > 0 ? o.queue_refill : 1;
   a.order = o.order;
   a.gscratch = m->d_gscratch;
@@ -546,11 +556,14 @@ extern "C" int kin_integrate_host(kin_mech *m, double *Y, double *T, const doubl
   if (rc) return rc;
   if (opt && (opt->h0 || opt->z0 || opt->h_first || opt->z_first || opt->order))
     return KIN_ERR_INVALID_ARG;
+  if (opt && opt->order_by != 0 && opt->order_by != 1) return KIN_ERR_INVALID_ARG;
+  if (opt && opt->order_by && n > INT32_MAX) return KIN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int ns = m->L.ns;
   if (n > m->h_cap) {
     if ((rc = grow(&m->h_Y, n * ns)) || (rc = grow(&m->h_T, n)) || (rc = grow(&m->h_P, n)) ||
-        (rc = grow(&m->h_status, n)) || (rc = grow(&m->h_cnt, n * KIN_NCOUNTERS))) {
+        (rc = grow(&m->h_status, n)) || (rc = grow(&m->h_cnt, n * KIN_NCOUNTERS)) ||
+        (rc = grow(&m->h_key, n)) || (rc = grow(&m->h_order, n))) {
       m->h_cap = 0;
       return rc;
     }
@@ -561,7 +574,19 @@ extern "C" int kin_integrate_host(kin_mech *m, double *Y, double *T, const doubl
   KIN_CUDA_TRY(cudaMemcpyAsync(m->h_Y, Y, sizeof(double) * n * ns, cudaMemcpyHostToDevice, st));
   KIN_CUDA_TRY(cudaMemcpyAsync(m->h_T, T, sizeof(double) * n, cudaMemcpyHostToDevice, st));
   KIN_CUDA_TRY(cudaMemcpyAsync(m->h_P, P, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  rc = kin_integrate_ex(m, m->h_Y, m->h_T, m->h_P, n, dt, rtol, atol, opt,
+  kin_options o;
+  if (opt) {
+    o = *opt;
+  } else {
+    kin_options_default(&o);
+  }
+  if (o.order_by == 1) {  // stiffness ordering into the entry's own buffers
+    rc = kin_order_states(m, m->h_Y, m->h_T, m->h_P, n, rtol, atol, KIN_KEY_STEP_HEURISTIC,
+                          m->h_key, m->h_order, stream);
+    if (rc) return rc;
+    o.order = m->h_order;
+  }
+  rc = kin_integrate_ex(m, m->h_Y, m->h_T, m->h_P, n, dt, rtol, atol, &o,
                         status ? m->h_status : nullptr, counters ? m->h_cnt : nullptr, stream);
   if (rc) return rc;
   KIN_CUDA_TRY(cudaMemcpyAsync(Y, m->h_Y, sizeof(double) * n * ns, cudaMemcpyDeviceToHost, st));

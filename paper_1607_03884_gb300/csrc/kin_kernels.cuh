@@ -83,10 +83,28 @@ __device__ void store_state(const Work<MAXN, LT> &w, const StepState &s, const K
   atomicMax(a.totals + 8, (unsigned long long)s.nstep);
 }
 
+// Launch bounds of the thread layouts: 64 threads per block, and optionally a
+// minimum of resident blocks per SM for the register allocator
+// (-DKIN_THREAD_MIN_BLOCKS=8 caps a thread at 128 registers).
+#ifdef KIN_THREAD_MIN_BLOCKS
+#define KIN_THREAD_BOUNDS __launch_bounds__(64, KIN_THREAD_MIN_BLOCKS)
+#else
+#define KIN_THREAD_BOUNDS __launch_bounds__(64)
+#endif
+
+// The thread layouts either stage the mechanism tables in shared memory per
+// block or read them through L1 (-DKIN_THREAD_TABLES_L1), leaving the unified
+// L1/shared memory to the per-thread workspace.
+#ifdef KIN_THREAD_TABLES_L1
+#define KIN_THREAD_VIEW(a, smem) make_view((a).L, (a).tab, (a).itab)
+#else
+#define KIN_THREAD_VIEW(a, smem) stage_tables((a).L, (a).tab, (a).itab, smem)
+#endif
+
 template <int MAXN, typename LT, bool FDJ>
-__global__ void __launch_bounds__(64) k_integrate_plain(KernelArgs a) {
+__global__ void KIN_THREAD_BOUNDS k_integrate_plain(KernelArgs a) {
   extern __shared__ double smem[];
-  const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
+  const MechView m = KIN_THREAD_VIEW(a, smem);
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= a.rp.n) return;
   const int64_t i = state_of(a, slot);
@@ -100,9 +118,9 @@ __global__ void __launch_bounds__(64) k_integrate_plain(KernelArgs a) {
 }
 
 template <int MAXN, typename LT, bool FDJ>
-__global__ void __launch_bounds__(64) k_integrate_queue(KernelArgs a) {
+__global__ void KIN_THREAD_BOUNDS k_integrate_queue(KernelArgs a) {
   extern __shared__ double smem[];
-  const MechView m = stage_tables(a.L, a.tab, a.itab, smem);
+  const MechView m = KIN_THREAD_VIEW(a, smem);
   const int N = m.ns;
   const int64_t n = a.rp.n;
   const unsigned FULL = 0xffffffffu;
@@ -258,17 +276,28 @@ int launch_t(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms
       return KIN_ERR_UNSUPPORTED;
     }
   }
+#ifdef KIN_THREAD_TABLES_L1
+  const size_t sm = 0;
+#else
   const size_t sm = smem_bytes(a.L);
+#endif
   const int block = o.block > 0 ? o.block : 64;
   if (block > 64 || block % 32) return KIN_ERR_INVALID_ARG;
+#ifdef KIN_THREAD_CARVEOUT
+  const int carve = KIN_THREAD_CARVEOUT;  // percent of the unified L1 given to shared memory
+#else
+  const int carve = -1;                   // driver default
+#endif
   if (o.layout == KIN_LAYOUT_PLAIN) {
     auto kern = k_integrate_plain<MAXN, LT, FDJ>;
     KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
     const int64_t grid = (a.rp.n + block - 1) / block;
     kern<<<(unsigned)grid, block, sm, st>>>(a);
   } else {
     auto kern = k_integrate_queue<MAXN, LT, FDJ>;
     KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
     int per_sm = o.grid_per_sm;
     if (per_sm <= 0) {
       KIN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm));

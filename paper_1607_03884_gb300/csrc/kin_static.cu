@@ -106,6 +106,7 @@ extern "C" int kin_integrate_static(const kin_mech_desc *desc, double *Y, double
   a.rp.h_first = nullptr;
   a.rp.z_first = nullptr;
   a.rp.stop_after = 0;
+  a.rp.hfixed = 0.0;
   a.refill_min = 1;
   a.order = nullptr;
   a.gscratch = nullptr;  // the default (QUEUE) layout needs no group slots

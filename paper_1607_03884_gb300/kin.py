@@ -51,7 +51,8 @@ class Options(C.Structure):
                 ("grid_per_sm", C.c_int32), ("transform_tol", C.c_int32),
                 ("queue_refill", C.c_int32), ("stop_after", C.c_int32), ("h0", C.c_void_p),
                 ("z0", C.c_void_p), ("h_first", C.c_void_p), ("z_first", C.c_void_p),
-                ("order", C.c_void_p), ("lanes", C.c_int32)]
+                ("order", C.c_void_p), ("lanes", C.c_int32), ("h_fixed", C.c_double),
+                ("order_by", C.c_int32)]
 
 
 _lib = None
@@ -129,7 +130,7 @@ def _stream(stream):
 
 def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7, block=0,
             grid_per_sm=0, transform_tol=True, queue_refill=0, stop_after=0, h0=None, z0=None,
-            h_first=None, z_first=None, order=None, lanes=0):
+            h_first=None, z_first=None, order=None, lanes=0, h_fixed=0.0, order_by=None):
     o = Options()
     _check(lib().kin_options_default(C.byref(o)), "kin_options_default")
     o.layout = {"plain": LAYOUT_PLAIN, "queue": LAYOUT_QUEUE, "warp": LAYOUT_WARP}[layout] \
@@ -147,6 +148,8 @@ def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7
     o.h0, o.z0, o.h_first, o.z_first = _ptr(h0), _ptr(z0), _ptr(h_first), _ptr(z_first)
     o.order = _ptr(order)
     o.lanes = int(lanes)
+    o.h_fixed = float(h_fixed)
+    o.order_by = {None: 0, "none": 0, "heuristic": 1}[order_by]
     return o
 
 

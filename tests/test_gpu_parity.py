@@ -446,6 +446,15 @@ def test_host_entry_matches_device_entry(h2):
     np.testing.assert_array_equal(Yh, Yd)
     np.testing.assert_array_equal(Th, Td)
     np.testing.assert_array_equal(cnt.T, cd)
+    # ordered inside the host entry: the same bits, counters by state
+    Yo, To = st.Y.copy(), st.T.copy()
+    cnt2 = np.zeros((8, st.n), dtype=np.int32)
+    mg.integrate_host(Yo, To, st.P.copy(), 1e-6, counters=cnt2, order_by="heuristic")
+    np.testing.assert_array_equal(Yo, Yd)
+    np.testing.assert_array_equal(To, Td)
+    np.testing.assert_array_equal(cnt2.T, cd)
+    with pytest.raises(kin.KinError):   # the device entry takes an explicit order
+        run_gpu(mg, st, 1e-6, order_by="heuristic")
 
 
 def test_default_entry_is_queue_fp64(h2):
@@ -625,3 +634,61 @@ def test_warp_layout_fd_jacobian_and_edge_sizes(ch4):
         assert eT <= RTOL_PARITY
         E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), np.concatenate([To[None], Yo[:-1]]))
         assert E.max() < 1.0, E.max()
+
+
+# ----------------------------------------------------------------------------
+# constant steps: parity and the convergence experiment (Sec. 2.3)
+# ----------------------------------------------------------------------------
+
+def test_fixed_steps_match_the_oracle(h2):
+    mech, mg, st = h2
+    sub = st.subset(np.arange(96))
+    dt, m = 1e-6, 200   # every one of these states converges at this step
+    Yo, To, co = O.integrate(mech, sub, dt, hfixed=dt / m)
+    for f32 in (False, True):
+        Yg, Tg, cg, sg = run_gpu(mg, sub, dt, layout="plain", h_fixed=dt / m, lu_fp32=f32)
+        assert np.all(sg == 0) and np.all(co[:, 7] == 0)
+        assert np.all(cg[:, 1] == m) and np.all(co[:, 1] == m)
+        assert np.all(cg[:, 2] == 0)                       # nothing rejected
+        assert np.all(cg[:, 4] == m)                       # a Jacobian per step
+        if not f32:   # the same step sequence; Newton counts equal up to rounding
+            assert np.mean(np.all(cg[:, :7] == co[:, :7], axis=1)) >= 0.95
+        eT, eY, _ = parity(Yg, Tg, Yo, To)
+        assert eT <= RTOL_PARITY and eY <= RTOL_PARITY, (f32, eT, eY)
+    with pytest.raises(kin.KinError):
+        run_gpu(mg, sub, dt, layout="warp", h_fixed=dt / m)
+    with pytest.raises(kin.KinError):
+        run_gpu(mg, sub, dt, layout="plain", h_fixed=-1.0)
+
+
+def test_constant_step_convergence_against_the_exact_solution(h2):
+    """The paper's verification (Sec. 2.3): constant-step Radau IIA on the
+    H2 problem at dt = 1e-6 s against a tight-tolerance reference (the
+    oracle at rtol 1e-13, atol 1e-20, untransformed), error E_i with the
+    atol 1e-10 / rtol 1e-6 weights.  The median error falls by more than
+    two orders of magnitude per decade of steps until it meets the
+    reference's own accuracy; every state converges from 128 steps on."""
+    mech, mg, st = h2
+    sub = st.subset(np.arange(0, st.n, 8))
+    dt = 1e-6
+    Yx, Tx, _ = O.integrate(mech, sub, dt, rtol=1e-13, atol=1e-20, transform_tol=False)
+    yx = np.concatenate([Tx[None], Yx[:-1]])
+    ms = np.array([32, 128, 512, 2048])
+    Es, oks = [], []
+    for m in ms:
+        Yg, Tg, cg, sg = run_gpu(mg, sub, dt, layout="plain", h_fixed=dt / m, nit=20)
+        assert np.all((sg == 0) | (sg == 5))      # only Newton failures at large steps
+        assert np.all(cg[sg == 0, 1] == m)
+        oks.append(sg == 0)
+        Es.append(O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), yx))
+    ok = np.logical_and.reduce(oks)
+    assert np.all(oks[1]) and np.all(oks[2]) and np.all(oks[3])
+    med = np.array([np.median(E[ok]) for E in Es])
+    mx = np.array([E[ok].max() for E in Es])
+    order = -np.diff(np.log10(med)) / np.diff(np.log10(ms))
+    print(f"\nconstant steps, {ok.sum()} of {sub.n} states converged at every count:")
+    for m, a, b, o in zip(ms, med, mx, oks):
+        print(f"  steps {m:5d}  converged {o.sum():4d}  median E {a:.3e}  max E {b:.3e}")
+    print("  observed orders", np.round(order, 2))
+    assert np.all(np.diff(med) < 0)
+    assert np.all(order >= 2.0) and order.mean() <= 6.0, order
