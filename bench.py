@@ -35,7 +35,7 @@ RTOL, ATOL = 1e-6, 1e-10
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dt", type=float, default=1e-4)
@@ -224,6 +224,7 @@ def run_ours(args, rank, world):
     clocks = clk.stop()
     tot = mg.stats()
     t_step = float(np.mean(times))
+    t_median = float(np.median(times))
     t_max = t_step
     if dist is not None:
         tt = torch.tensor([t_step], device="cuda")
@@ -272,17 +273,50 @@ def run_ours(args, rank, world):
             t0 = time.perf_counter()
             mg.integrate_host(Yp, Tp, Ph, args.dt, RTOL, ATOL, stream=stream, **hopt)
             te.append(time.perf_counter() - t0)
+        # warp divergence D = 1 - sum d / (32 max d) per warp of 32 consecutive
+        # slots (Sec. 3.3), from the per-state step counts d; a state's steps do
+        # not depend on its slot, so one counted run gives D for any order
+        Y.copy_(Y0)
+        T.copy_(T0)
+        cnt = torch.zeros((8, n), dtype=torch.int32, device="cuda")
+        mg.integrate(Y, T, P, args.dt, RTOL, ATOL, stream=stream, counters=cnt,
+                     **{k: v for k, v in opt.items() if k != "order"})
+        mg.order_states(Y0, T0, P, RTOL, ATOL, key=key_buf, order=order_buf, stream=stream)
+        torch.cuda.synchronize()
+        d = cnt[0].cpu().numpy().astype(np.float64)
+
+        def warp_div(v):
+            w = v[: v.size // 32 * 32].reshape(-1, 32)
+            return float(np.mean(1.0 - w.sum(1) / (32.0 * np.maximum(w.max(1), 1.0))))
+        out["divergence"] = {"D_mean_in_input_order": warp_div(d),
+                             "D_mean_ordered": warp_div(d[order_buf.cpu().numpy()]),
+                             "steps_mean": float(d.mean()), "steps_max": int(d.max())}
         out["e2e"] = {"value": n / float(np.mean(te)), "unit": "states/s",
                       "h2d_bytes_per_step": int(n * (mech.ns + 2) * 8),
                       "d2h_bytes_per_step": int(n * (mech.ns + 1) * 8)}
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
-    return dict(value=value, t_step=t_max, times=times, wall=wall, clocks=clocks, tot=tot,
+    return dict(value=value, t_step=t_max, t_median=t_median, times=times, wall=wall,
+                clocks=clocks, tot=tot,
                 f64=f64, f32=f32, n=n, mech=mech, st=st, extras=out)
 
 
-def cpu_baseline(sample, dt, workload=WORKLOAD):
+def cpu_model():
+    """The host CPU's name as the OS reports it (x86 'model name' or Arm 'CPU part')."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            txt = fh.read()
+    except OSError:
+        return None
+    for key in ("model name", "CPU part"):
+        for line in txt.splitlines():
+            if line.startswith(key):
+                return f"{key}: {line.split(':', 1)[1].strip()}"
+    return None
+
+
+def cpu_baseline(sample, dt, workload=WORKLOAD, one_core=True):
     from oracle import oracle as O
     from paper_1607_03884_gb300 import synth
     mech, st, _ = synth.workload(workload)
@@ -292,9 +326,15 @@ def cpu_baseline(sample, dt, workload=WORKLOAD):
     t0 = time.perf_counter()
     O.integrate(mech, sub, dt, rtol=RTOL, atol=ATOL)
     el = time.perf_counter() - t0
-    return {"value": sample / el, "unit": "states/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{sample} states drawn (seed 1) from the {workload} workload, dt={dt:g}",
-            "seconds": el}
+    out = {"value": sample / el, "unit": "states/s", "cores": O.num_threads(), "kind": "oracle",
+           "sample": f"{sample} states drawn (seed 1) from the {workload} workload, dt={dt:g}",
+           "seconds": el, "cpu": cpu_model()}
+    if one_core:  # the same oracle on one thread, over a quarter of the sample
+        m = max(16, sample // 4)
+        t0 = time.perf_counter()
+        O.integrate(mech, sub.subset(np.arange(m)), dt, rtol=RTOL, atol=ATOL, nthreads=1)
+        out["value_1core"] = m / (time.perf_counter() - t0)
+    return out
 
 
 def kernel_digest():
@@ -349,7 +389,8 @@ def main():
             return
         reps = []
         for _ in range(args.warmup + args.steps):
-            reps.append(cpu_baseline(max(64, args.cpu_sample // 4), args.dt, args.workload))
+            reps.append(cpu_baseline(max(64, args.cpu_sample // 4), args.dt, args.workload,
+                                     one_core=False))
         vals = [r["value"] for r in reps[args.warmup:]]
         v = float(np.mean(vals))
         cb = dict(reps[-1])
@@ -396,7 +437,10 @@ def main():
         "roofline": roof,
         "cpu_baseline": cb,
         "e2e": ex.get("e2e"),
-        "gpu_launches": args.steps,
+        "ms_per_step_median": 1e3 * r["t_median"],
+        # per step: the integration kernel, plus the six ordering kernels
+        # (init, key, min/max, histogram, scan, scatter) when ordering
+        "gpu_launches": args.steps * (1 + (6 if args.order != "none" else 0)),
         "graph": bool(args.graph),
         "clocks": r["clocks"],
         "plain_fp64_states_per_s": ex.get("plain_fp64_states_per_s"),
@@ -404,6 +448,7 @@ def main():
                           if ex.get("plain_fp64_states_per_s") else None),
         "error_vs_plain_fp64": ex.get("error_vs_plain_fp64"),
         "per_dt": ex.get("per_dt"),
+        "divergence": ex.get("divergence"),
         "counters": {k: int(v) for k, v in r["tot"].items()},
     }
     print(json.dumps(line))

@@ -586,6 +586,7 @@ extern "C" int kin_integrate_host(kin_mech *m, double *Y, double *T, const doubl
     if (rc) return rc;
     o.order = m->h_order;
   }
+  o.order_by = 0;  // handled here; the device entry takes the explicit order
   rc = kin_integrate_ex(m, m->h_Y, m->h_T, m->h_P, n, dt, rtol, atol, &o,
                         status ? m->h_status : nullptr, counters ? m->h_cnt : nullptr, stream);
   if (rc) return rc;

@@ -83,22 +83,31 @@ __device__ void store_state(const Work<MAXN, LT> &w, const StepState &s, const K
   atomicMax(a.totals + 8, (unsigned long long)s.nstep);
 }
 
-// Launch bounds of the thread layouts: 64 threads per block, and optionally a
-// minimum of resident blocks per SM for the register allocator
-// (-DKIN_THREAD_MIN_BLOCKS=8 caps a thread at 128 registers).
-#ifdef KIN_THREAD_MIN_BLOCKS
+// Tuning of the thread layouts (measured on 2^18 H2 states; the per-thread
+// workspace spills, so latency hiding matters more than spill volume):
+//   * 64 threads per block and at least KIN_THREAD_MIN_BLOCKS resident blocks
+//     per SM, which caps a thread's registers (20: 48 registers, 40 warps per
+//     SM; 0 leaves the allocator free: 168 registers, 12 warps);
+//   * the mechanism tables read through L1 rather than staged in shared
+//     memory per block (-DKIN_THREAD_TABLES_SMEM stages them), with the
+//     unified L1/shared memory split towards L1 (KIN_THREAD_CARVEOUT, percent
+//     given to shared memory; -1 = driver default).
+// Together: 144k -> 178k states/s (FP32 matrices) and 106k -> 131k (FP64).
+#ifndef KIN_THREAD_MIN_BLOCKS
+#define KIN_THREAD_MIN_BLOCKS 20
+#endif
+#if KIN_THREAD_MIN_BLOCKS > 0
 #define KIN_THREAD_BOUNDS __launch_bounds__(64, KIN_THREAD_MIN_BLOCKS)
 #else
 #define KIN_THREAD_BOUNDS __launch_bounds__(64)
 #endif
-
-// The thread layouts either stage the mechanism tables in shared memory per
-// block or read them through L1 (-DKIN_THREAD_TABLES_L1), leaving the unified
-// L1/shared memory to the per-thread workspace.
-#ifdef KIN_THREAD_TABLES_L1
-#define KIN_THREAD_VIEW(a, smem) make_view((a).L, (a).tab, (a).itab)
-#else
+#ifndef KIN_THREAD_CARVEOUT
+#define KIN_THREAD_CARVEOUT 0
+#endif
+#ifdef KIN_THREAD_TABLES_SMEM
 #define KIN_THREAD_VIEW(a, smem) stage_tables((a).L, (a).tab, (a).itab, smem)
+#else
+#define KIN_THREAD_VIEW(a, smem) make_view((a).L, (a).tab, (a).itab)
 #endif
 
 template <int MAXN, typename LT, bool FDJ>
@@ -276,18 +285,14 @@ int launch_t(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms
       return KIN_ERR_UNSUPPORTED;
     }
   }
-#ifdef KIN_THREAD_TABLES_L1
-  const size_t sm = 0;
-#else
+#ifdef KIN_THREAD_TABLES_SMEM
   const size_t sm = smem_bytes(a.L);
+#else
+  const size_t sm = 0;
 #endif
   const int block = o.block > 0 ? o.block : 64;
   if (block > 64 || block % 32) return KIN_ERR_INVALID_ARG;
-#ifdef KIN_THREAD_CARVEOUT
   const int carve = KIN_THREAD_CARVEOUT;  // percent of the unified L1 given to shared memory
-#else
-  const int carve = -1;                   // driver default
-#endif
   if (o.layout == KIN_LAYOUT_PLAIN) {
     auto kern = k_integrate_plain<MAXN, LT, FDJ>;
     KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
