@@ -146,6 +146,23 @@ class ClockSampler:
 # GPU leg
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(t, dist=None, device="cpu"):
+    """The slowest rank's step time (every rank gets it); t itself on one rank."""
+    if dist is None:
+        return float(t)
+    import torch
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(n_per_rank, world, t_max):
+    """States per second of the whole job: every rank integrates its own n
+    states (weak scaling, no collective on the data path), the job lasts as
+    long as its slowest rank."""
+    return n_per_rank * world / t_max
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1607_03884_gb300 import kin, synth
@@ -225,12 +242,8 @@ def run_ours(args, rank, world):
     tot = mg.stats()
     t_step = float(np.mean(times))
     t_median = float(np.median(times))
-    t_max = t_step
-    if dist is not None:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = n * world / t_max
+    t_max = max_over_ranks(t_step, dist, "cuda")
+    value = whole_job_rate(n, world, t_max)
     f64, f32 = algorithmic_flops(tot, ops, bool(args.fp32))
 
     out = {"tune": tune, "opt": {k: v for k, v in opt.items()}}
