@@ -457,7 +457,7 @@ int kin::launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t
                          int sms) {
   if (o.layout == KIN_LAYOUT_WARP && o.lanes != 0 && o.lanes != 32)
     return o.lu_fp32 ? kin_launch_grpf(a, o, st, sms) : kin_launch_grpd(a, o, st, sms);
-  if (a.L.ns <= 16 && o.layout != KIN_LAYOUT_WARP)
+  if (a.L.ns <= SMALL_MAXN && o.layout != KIN_LAYOUT_WARP)
     return o.lu_fp32 ? kin_launch_16f(a, o, st, sms) : kin_launch_16d(a, o, st, sms);
   return o.lu_fp32 ? kin_launch_64f(a, o, st, sms) : kin_launch_64d(a, o, st, sms);
 }

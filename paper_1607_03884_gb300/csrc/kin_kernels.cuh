@@ -23,6 +23,13 @@ __host__ __device__ inline size_t smem_bytes(const MechLayout &L) {
   return sizeof(double) * (size_t)L.nd + sizeof(int) * (size_t)L.ni;
 }
 
+// Species capacity of the small-mechanism thread kernels: the per-thread
+// workspace is sized for it (a smaller one spills less).
+#ifndef KIN_SMALL_MAXN
+#define KIN_SMALL_MAXN 16
+#endif
+constexpr int SMALL_MAXN = KIN_SMALL_MAXN;
+
 struct KernelArgs {
   MechLayout L;
   const double *tab;

@@ -1,6 +1,6 @@
-// Radau kernels for up to 16 species with double Newton matrices.
+// Radau kernels for up to SMALL_MAXN (16) species with double Newton matrices.
 #include "kin_kernels.cuh"
 
 namespace kin {
-KIN_DEFINE_TU(16d, 16, double)
+KIN_DEFINE_TU(16d, SMALL_MAXN, double)
 }  // namespace kin

@@ -1,6 +1,6 @@
-// Radau kernels for up to 16 species with float Newton matrices.
+// Radau kernels for up to SMALL_MAXN (16) species with float Newton matrices.
 #include "kin_kernels.cuh"
 
 namespace kin {
-KIN_DEFINE_TU(16f, 16, float)
+KIN_DEFINE_TU(16f, SMALL_MAXN, float)
 }  // namespace kin
