@@ -246,11 +246,14 @@ int kin_get_stats(kin_mech *m, int64_t *out);
  *     norms of y and f(y), tolerances transformed as in the integrator): one
  *     right-hand side per state from Y, T, P (dev, as kin_integrate); a state
  *     whose rates are not finite gets -inf.
- *   key_mode KIN_KEY_GIVEN: key is read as given (for example the predictor's
- *     ln h0); Y, T, P, rtol and atol are not used and may be NULL/0.
+ *   key_mode KIN_KEY_GIVEN: key is read as given; Y, T, P, rtol and atol
+ *     are not used and may be NULL/0.
+ *   key_mode KIN_KEY_GIVEN_LOG: as KIN_KEY_GIVEN, sorted by the natural log
+ *     of a positive key (for example the predictor's h0 from
+ *     kin_mlp_predict); a zero key goes first and a negative one last.
  * n <= 2^31 - 1.  Asynchronous on stream; uses a workspace owned by the
  * mechanism, so calls on one kin_mech must not overlap. */
-enum { KIN_KEY_GIVEN = 0, KIN_KEY_STEP_HEURISTIC = 1 };
+enum { KIN_KEY_GIVEN = 0, KIN_KEY_STEP_HEURISTIC = 1, KIN_KEY_GIVEN_LOG = 2 };
 int kin_order_states(kin_mech *m, const double *Y, const double *T, const double *P, int64_t n,
                      double rtol, double atol, int32_t key_mode, double *key, int32_t *order,
                      void *stream);

@@ -615,7 +615,9 @@ extern "C" int kin_order_states(kin_mech *m, const double *Y, const double *T, c
                                 int64_t n, double rtol, double atol, int32_t key_mode,
                                 double *key, int32_t *order, void *stream) {
   if (!m || n < 0 || n > INT32_MAX) return KIN_ERR_INVALID_ARG;
-  if (key_mode != KIN_KEY_GIVEN && key_mode != KIN_KEY_STEP_HEURISTIC) return KIN_ERR_INVALID_ARG;
+  if (key_mode != KIN_KEY_GIVEN && key_mode != KIN_KEY_STEP_HEURISTIC &&
+      key_mode != KIN_KEY_GIVEN_LOG)
+    return KIN_ERR_INVALID_ARG;
   if (n == 0) return KIN_OK;
   if (!key || !order) return KIN_ERR_INVALID_ARG;
   const bool compute = key_mode == KIN_KEY_STEP_HEURISTIC;
@@ -628,8 +630,9 @@ extern "C" int kin_order_states(kin_mech *m, const double *Y, const double *T, c
   KIN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // the integrator's default tolerance transform (Hairer-Wanner)
   const double r = 0.1 * std::pow(rtol, 2.0 / 3.0), at = compute ? r * (atol / rtol) : 0.0;
-  return launch_order(m->L, m->d_tab, m->d_itab, Y, T, P, n, r, at, compute, key, order,
-                      m->d_order_ws, (cudaStream_t)stream, sms);
+  return launch_order(m->L, m->d_tab, m->d_itab, Y, T, P, n, r, at, compute,
+                      key_mode == KIN_KEY_GIVEN_LOG, key, order, m->d_order_ws,
+                      (cudaStream_t)stream, sms);
 }
 
 extern "C" int kin_rhs(kin_mech *m, const double *y, const double *P, int64_t n, double *f,

@@ -19,6 +19,6 @@ int launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t st, 
 size_t order_workspace_bytes();
 int launch_order(const MechLayout &L, const double *tab, const int *itab, const double *Y,
                  const double *T, const double *P, int64_t n, double rtol, double atol,
-                 bool compute_key, double *key, int32_t *order, void *ws, cudaStream_t st,
-                 int sms);
+                 bool compute_key, bool log_key, double *key, int32_t *order, void *ws,
+                 cudaStream_t st, int sms);
 }  // namespace kin

@@ -7,7 +7,7 @@
 // first-step size: either the Hairer-Wanner starting-step heuristic
 // (0.01 d0/d1 with d0 = ||y||, d1 = ||f(y)|| in the weighted RMS norm, one
 // right-hand side per state) or a key the caller supplies (the predictor's
-// ln h0).  The permutation is a counting sort of the key into 4096
+// h0, taken by its logarithm).  The permutation is a counting sort of the key into 4096
 // equal-width bins between its minimum and maximum: min/max, histogram,
 // exclusive scan, scatter.  The order inside a bin is not specified; the
 // integration of a state does not depend on the slot that carries it.
@@ -66,11 +66,16 @@ __global__ void k_order_init(unsigned long long *ws) {
   for (int b = threadIdx.x; b < ORDER_BINS; b += blockDim.x) cnt[b] = 0u;
 }
 
-__global__ void k_order_minmax(const double *key, int64_t n, unsigned long long *ws) {
+// the sort key of state i: the key itself, or its natural logarithm
+__device__ __forceinline__ double key_at(const double *key, int64_t i, bool logk) {
+  return logk ? log(key[i]) : key[i];  // log: 0 -> -inf (first), negative -> NaN (last)
+}
+
+__global__ void k_order_minmax(const double *key, bool logk, int64_t n, unsigned long long *ws) {
   unsigned long long lo = ~0ull, hi = 0ull;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double k = key[i];
+    const double k = key_at(key, i, logk);
     if (!isfinite(k)) continue;
     const unsigned long long u = key_bits(k);
     lo = u < lo ? u : lo;
@@ -98,7 +103,7 @@ __device__ __forceinline__ int order_bin(double k, double lo, double span) {
   return b < ORDER_BINS ? b : ORDER_BINS - 1;
 }
 
-__global__ void k_order_hist(const double *key, int64_t n, unsigned long long *ws) {
+__global__ void k_order_hist(const double *key, bool logk, int64_t n, unsigned long long *ws) {
   __shared__ unsigned int h[ORDER_BINS];
   for (int b = threadIdx.x; b < ORDER_BINS; b += blockDim.x) h[b] = 0u;
   __syncthreads();
@@ -106,7 +111,7 @@ __global__ void k_order_hist(const double *key, int64_t n, unsigned long long *w
   const double span = hi - lo;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&h[order_bin(key[i], lo, span)], 1u);
+    atomicAdd(&h[order_bin(key_at(key, i, logk), lo, span)], 1u);
   __syncthreads();
   unsigned int *cnt = reinterpret_cast<unsigned int *>(ws + 2);
   for (int b = threadIdx.x; b < ORDER_BINS; b += blockDim.x)
@@ -139,14 +144,14 @@ __global__ void k_order_scan(unsigned long long *ws) {
   }
 }
 
-__global__ void k_order_scatter(const double *key, int64_t n, unsigned long long *ws,
-                                int32_t *order) {
+__global__ void k_order_scatter(const double *key, bool logk, int64_t n,
+                                unsigned long long *ws, int32_t *order) {
   const double lo = bits_key(ws[0]), hi = bits_key(ws[1]);
   const double span = hi - lo;
   unsigned int *cur = reinterpret_cast<unsigned int *>(ws + 2);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned int pos = atomicAdd(&cur[order_bin(key[i], lo, span)], 1u);
+    const unsigned int pos = atomicAdd(&cur[order_bin(key_at(key, i, logk), lo, span)], 1u);
     order[pos] = (int32_t)i;
   }
 }
@@ -157,8 +162,8 @@ size_t order_workspace_bytes() {
 
 int launch_order(const MechLayout &L, const double *tab, const int *itab, const double *Y,
                  const double *T, const double *P, int64_t n, double rtol, double atol,
-                 bool compute_key, double *key, int32_t *order, void *ws_v, cudaStream_t st,
-                 int sms) {
+                 bool compute_key, bool log_key, double *key, int32_t *order, void *ws_v,
+                 cudaStream_t st, int sms) {
   unsigned long long *ws = static_cast<unsigned long long *>(ws_v);
   k_order_init<<<1, 1024, 0, st>>>(ws);
   if (compute_key) {
@@ -178,10 +183,11 @@ int launch_order(const MechLayout &L, const double *tab, const int *itab, const 
   }
   const int64_t want = (n + 255) / 256;
   const unsigned grid = (unsigned)(want < 4 * (int64_t)sms ? (want > 0 ? want : 1) : 4 * sms);
-  k_order_minmax<<<grid, 256, 0, st>>>(key, n, ws);
-  k_order_hist<<<grid, 256, 0, st>>>(key, n, ws);
+  const bool lg = log_key && !compute_key;
+  k_order_minmax<<<grid, 256, 0, st>>>(key, lg, n, ws);
+  k_order_hist<<<grid, 256, 0, st>>>(key, lg, n, ws);
   k_order_scan<<<1, 1024, 0, st>>>(ws);
-  k_order_scatter<<<grid, 256, 0, st>>>(key, n, ws, order);
+  k_order_scatter<<<grid, 256, 0, st>>>(key, lg, n, ws, order);
   KIN_CUDA_TRY(cudaGetLastError());
   return KIN_OK;
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libkin.so")
 KIN_OK, KIN_ERR_INVALID_ARG, KIN_ERR_CUDA, KIN_ERR_NOMEM, KIN_ERR_MECH = 0, 1, 2, 3, 4
 KIN_ERR_STATE_FAILED, KIN_ERR_UNSUPPORTED = 5, 6
 LAYOUT_PLAIN, LAYOUT_QUEUE, LAYOUT_WARP = 0, 1, 2
-KEY_GIVEN, KEY_STEP_HEURISTIC = 0, 1
+KEY_GIVEN, KEY_STEP_HEURISTIC, KEY_GIVEN_LOG = 0, 1, 2
 COUNTER_NAMES = ("nstep", "naccpt", "nrejct", "nfcn", "njac", "ndec", "nsol", "status")
 MAX_SPECIES = 64
 
@@ -291,15 +291,16 @@ class Mechanism:
                     grid_per_sm=best.grid_per_sm, lanes=best.lanes), secs.tolist()
 
     def order_states(self, Y, T, P, rtol=1e-6, atol=1e-10, *, key=None, given_key=None,
-                     order=None, stream=None):
+                     log_key=False, order=None, stream=None):
         """kin_order_states: (order, key) device tensors, order an int32
         permutation that sorts the key ascending (stiffest first).  With
         given_key (float64 [n], e.g. the predictor's ln h0) that key is used
         as is; otherwise the starting-step heuristic's ln h0 is computed into
-        key (a new tensor when key is None).  order: optional output buffer."""
+        key (a new tensor when key is None).  log_key: sort a positive given key
+        (e.g. the predictor's h0) by its logarithm.  order: optional output."""
         import torch
         if given_key is not None:
-            key, mode = given_key, KEY_GIVEN
+            key, mode = given_key, (KEY_GIVEN_LOG if log_key else KEY_GIVEN)
         else:
             mode = KEY_STEP_HEURISTIC
         n = int(T.shape[0]) if T is not None else int(key.shape[0])

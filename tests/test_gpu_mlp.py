@@ -118,3 +118,42 @@ def test_feature_target_and_prediction_kernels():
     h0n = h0.cpu().numpy()
     assert np.all(np.isfinite(h0n)) and np.all(h0n <= 1e-4) and np.all(h0n >= 1e-14)
     assert np.all(np.isfinite(z0.cpu().numpy()))
+
+
+def test_trained_predictor_removes_steps_at_equal_error():
+    """What the learned part gains: a predictor trained on integrator-made
+    targets (CH4-like states, WARP layout, FP32 matrices) gives a first step
+    that removes steps against the starting-step heuristic, and the results
+    stay as close to the exact solution (oracle at rtol 1e-13) as without it."""
+    from oracle import oracle as O
+    from paper_1607_03884_gb300 import learned
+    mech = synth.make_mechanism("ch4")
+    tr = synth.make_states(mech, 1 << 15, seed=47, T_range=(800.0, 2600.0))
+    te = synth.make_states(mech, 1 << 12, seed=46, T_range=(800.0, 2600.0))
+    mg = kin.Mechanism(mech)
+    dt = 1e-4
+    pred, info = learned.train(mech, mg, tr, dt, width=256, epochs=8, batch=1024, layout="warp")
+    assert info["samples"] > 0.9 * tr.n
+    assert info["history"][-1] < info["history"][0]
+    Y, T, P = (torch.from_numpy(a).cuda() for a in (te.Y, te.T, te.P))
+    runs = {}
+    for tag in ("none", "predicted"):
+        kw = {}
+        if tag == "predicted":
+            kw["h0"], _ = pred.predict(Y, T, P, dt)
+        Yw, Tw = Y.clone(), T.clone()
+        mg.integrate(Yw, Tw, P, dt, layout="warp", lu_fp32=True, **kw)
+        torch.cuda.synchronize()
+        runs[tag] = (Yw.cpu().numpy(), Tw.cpu().numpy(), mg.stats())
+    s0, s1 = runs["none"][2], runs["predicted"][2]
+    assert s0["failed"] == 0 and s1["failed"] == 0
+    assert s1["nstep"] < 0.99 * s0["nstep"], (s1["nstep"], s0["nstep"])
+    idx = np.arange(0, te.n, te.n // 16)
+    Yx, Tx, _ = O.integrate(mech, te.subset(idx), dt, rtol=1e-13, atol=1e-20)
+    yx = np.concatenate([Tx[None], Yx[:-1]])
+    E = {tag: O.error_norm(np.concatenate([r[1][idx][None], r[0][:-1, idx]]), yx)
+         for tag, r in runs.items()}
+    print(f"\nsteps/state {s0['nstep'] / te.n:.2f} -> {s1['nstep'] / te.n:.2f}; "
+          f"E vs exact max {E['none'].max():.3g} -> {E['predicted'].max():.3g}")
+    assert E["predicted"].max() <= max(10.0 * E["none"].max(), 30.0)
+    assert np.median(E["predicted"]) <= max(3.0 * np.median(E["none"]), 1.0)

@@ -348,6 +348,11 @@ def test_order_states_sorts_by_the_step_heuristic(h2):
     o2 = o2.cpu().numpy()
     np.testing.assert_array_equal(np.sort(o2), np.arange(n))
     assert np.all(np.diff(-k[o2]) >= -width * (1 + 1e-9))
+    # a positive key sorted by its logarithm: exp(key) gives the same bins
+    o3, _ = mg.order_states(None, None, None, given_key=torch.exp(key), log_key=True)
+    o3 = o3.cpu().numpy()
+    np.testing.assert_array_equal(np.sort(o3), np.arange(n))
+    assert np.all(np.diff(k[o3]) >= -width * (1 + 1e-9))
 
 
 def test_ordered_integration_gives_the_same_bits(h2):
