@@ -228,6 +228,13 @@ struct JacScratch {
   double dcp[MAXN];
 };
 
+// Unroll factor of the per-species and per-reaction loops of chem_eval: more
+// independent FP64 chains in flight per thread (a build-time tuning knob).
+#ifndef KIN_RHS_UNROLL
+#define KIN_RHS_UNROLL 1
+#endif
+constexpr int RHS_UNROLL = KIN_RHS_UNROLL;
+
 template <int MAXN, typename JT>
 __device__ __noinline__ int chem_eval(const MechView &m, double P, const double *y,
                                       double *f, JT *J, bool wantJ, ChemScratch<MAXN> &w,
@@ -245,6 +252,7 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
   const double rho = P / (RU * T * S);
   const double logT = log(T), invT = 1.0 / T;
   double cpm = 0.0, dcpm = 0.0;
+#pragma unroll RHS_UNROLL
   for (int k = 0; k < ns; ++k) {
     const double Yk = (k < in) ? y[1 + k] : Yin;
     w.C[k] = rho * Yk * m.invW[k];
@@ -273,6 +281,7 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
   }
   const double Ctot = rho * S;
   const double lnPf = 2.5003366899611787 - logT;  // ln(Patm / Ru) - ln T
+#pragma unroll RHS_UNROLL
   for (int i = 0; i < m.nr; ++i) {
     const int meta = m.meta[i];
     const int *sl = m.slot + 6 * i;
