@@ -339,6 +339,13 @@ int kin_mlp_grad(kin_mlp *net, const float *X, const float *T, int64_t M, float 
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) on a minibatch. */
 int kin_mlp_train_step(kin_mlp *net, const float *X, const float *T, int64_t M, float lr,
                        float *loss_out, void *stream);
+/* The same step on the minibatch rows[0..M) (dev int32) of a training set
+ * X dev [R][din], T dev [R][dout]: the library gathers the rows itself.  An
+ * index outside [0, R) contributes a zero row.  The gather buffers belong to
+ * the network and grow with M. */
+int kin_mlp_train_step_rows(kin_mlp *net, const float *X, const float *T, int64_t R,
+                            const int32_t *rows, int64_t M, float lr, float *loss_out,
+                            void *stream);
 /* Column means and standard deviations (floored at 1e-12) of X [M][d]. */
 int kin_moments(const float *X, int64_t M, int32_t d, float *mean, float *stdv, void *stream);
 /* Network inputs for n states (Y dev [ns][n], T, P dev [n], all FP64):

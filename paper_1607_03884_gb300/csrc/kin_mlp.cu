@@ -134,6 +134,18 @@ __global__ void k_bias_act(int64_t M, int N, const float *C, const float *b, flo
   if (hb) hb[i] = __float2bfloat16(h);
 }
 
+// gather rows of a [R][d] set: dst[r] = src[rows[r]]; an index outside
+// [0, R) gives a zero row
+__global__ void k_gather_rows(int64_t M, int d, const float *src, int64_t R,
+                              const int32_t *rows, float *dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * d) return;
+  const int64_t r = i / d;
+  const int c = (int)(i % d);
+  const int32_t s = rows[r];
+  dst[i] = (s >= 0 && (int64_t)s < R) ? src[(int64_t)s * d + c] : 0.0f;
+}
+
 // pad/convert an input block [M][din] f32 -> [M][ld] (f32 and bf16), zero pad
 __global__ void k_pack_input(int64_t M, int din, int ld, const float *X, float *xf,
                              __nv_bfloat16 *xb) {
@@ -285,11 +297,15 @@ struct kin_mlp {
   int64_t cap = 0;
   float *xf = nullptr, *a[LAYERS] = {}, *hf[LAYERS] = {}, *C = nullptr, *g = nullptr,
         *dH = nullptr, *y = nullptr, *loss = nullptr;
+  float *xg = nullptr, *tg = nullptr;  // gathered minibatch rows (train_step_rows)
   __nv_bfloat16 *xb = nullptr, *hb[LAYERS] = {}, *gb = nullptr;
 };
 
 static int mlp_reserve(kin_mlp *n, int64_t rows) {
   if (rows <= n->cap) return KIN_OK;
+  cudaFree(n->xg);
+  cudaFree(n->tg);
+  n->xg = n->tg = nullptr;
   cudaFree(n->xf);
   cudaFree(n->xb);
   cudaFree(n->C);
@@ -303,6 +319,8 @@ static int mlp_reserve(kin_mlp *n, int64_t rows) {
   }
   n->cap = 0;
   const int64_t wmax = n->width > n->doutp ? n->width : n->doutp;
+  KIN_CUDA_TRY(cudaMalloc(&n->xg, sizeof(float) * rows * n->din));
+  KIN_CUDA_TRY(cudaMalloc(&n->tg, sizeof(float) * rows * n->dout));
   KIN_CUDA_TRY(cudaMalloc(&n->xf, sizeof(float) * rows * n->dinp));
   KIN_CUDA_TRY(cudaMalloc(&n->xb, sizeof(__nv_bfloat16) * rows * n->dinp));
   KIN_CUDA_TRY(cudaMalloc(&n->C, sizeof(float) * rows * wmax));
@@ -457,6 +475,8 @@ extern "C" void kin_mlp_destroy(kin_mlp *n) {
   cudaFree(n->mask);
   cudaFree(n->wb);
   cudaFree(n->loss);
+  cudaFree(n->xg);
+  cudaFree(n->tg);
   cudaFree(n->xf);
   cudaFree(n->xb);
   cudaFree(n->C);
@@ -581,6 +601,19 @@ extern "C" int kin_mlp_train_step(kin_mlp *n, const float *X, const float *T, in
   if (loss_out)
     KIN_CUDA_TRY(cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
   return KIN_OK;
+}
+
+extern "C" int kin_mlp_train_step_rows(kin_mlp *n, const float *X, const float *T, int64_t R,
+                                       const int32_t *rows, int64_t M, float lr, float *loss_out,
+                                       void *stream) {
+  if (!n || M < 1 || R < 1 || !X || !T || !rows || !(lr > 0.0f)) return KIN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = mlp_reserve(n, M);
+  if (rc) return rc;
+  k_gather_rows<<<blocks(M * n->din), 256, 0, st>>>(M, n->din, X, R, rows, n->xg);
+  k_gather_rows<<<blocks(M * n->dout), 256, 0, st>>>(M, n->dout, T, R, rows, n->tg);
+  KIN_CUDA_TRY(cudaGetLastError());
+  return kin_mlp_train_step(n, n->xg, n->tg, M, lr, loss_out, stream);
 }
 
 extern "C" int kin_moments(const float *X, int64_t M, int32_t d, float *mean, float *stdv,

@@ -29,7 +29,7 @@ EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integra
            "kin_integrate_static", "kin_mlp_create", "kin_mlp_destroy", "kin_mlp_num_params",
            "kin_mlp_get_params", "kin_mlp_set_params", "kin_mlp_forward", "kin_mlp_grad",
            "kin_mlp_train_step", "kin_moments", "kin_mlp_features", "kin_mlp_targets",
-           "kin_mlp_predict", "kin_autotune", "kin_order_states")
+           "kin_mlp_predict", "kin_autotune", "kin_order_states", "kin_mlp_train_step_rows")
 
 
 class KinError(RuntimeError):
@@ -96,6 +96,7 @@ def lib():
             L.kin_mlp_forward.argtypes = [vp, vp, vp, i64, vp]
             L.kin_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
             L.kin_mlp_train_step.argtypes = [vp, vp, vp, i64, C.c_float, vp, vp]
+            L.kin_mlp_train_step_rows.argtypes = [vp, vp, vp, i64, vp, i64, C.c_float, vp, vp]
             L.kin_moments.argtypes = [vp, i64, i32, vp, vp, vp]
             L.kin_mlp_features.argtypes = [i32, vp, vp, vp, i64, d, vp, vp, vp, vp]
             L.kin_mlp_targets.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp]
@@ -391,6 +392,13 @@ class MLP:
     def train_step(self, X, T, lr, loss_out=None, stream=None):
         _check(lib().kin_mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),
                                         _ptr(loss_out), _stream(stream)), "kin_mlp_train_step")
+
+    def train_step_rows(self, X, T, rows, lr, loss_out=None, stream=None):
+        """Adam step on the rows (device int32 tensor) of the training set X, T."""
+        _check(lib().kin_mlp_train_step_rows(self._h, _ptr(X), _ptr(T), int(X.shape[0]),
+                                             _ptr(rows), int(rows.shape[0]), float(lr),
+                                             _ptr(loss_out), _stream(stream)),
+               "kin_mlp_train_step_rows")
 
     def predict(self, ns, Y, T, P, dt, norm, h0=None, z0=None, stream=None):
         """norm: dict of device float tensors in_mean, in_std, out_mean, out_std."""

@@ -111,18 +111,17 @@ def train(mech, mg, states, dt, *, width=256, epochs=4, batch=4096, lr=2e-3, see
     Ts = torch.empty_like(Tg)
     kin.targets(3 * ns, h, z, Ts, norm["out_mean"], norm["out_std"])
     net = kin.MLP(din, width, dout, precision=precision, seed=seed)
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(seed)
+    rng = np.random.default_rng(seed)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     history = []
     steps = max(1, n // batch)
     for ep in range(epochs):
-        perm = torch.randperm(n, device="cuda", generator=gen)
+        # a host-drawn permutation per epoch; the library gathers each batch
+        perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
         lr_ep = lr * (0.5 ** ep)
         acc = 0.0
         for s in range(steps):
-            sel = perm[s * batch:(s + 1) * batch]
-            net.train_step(Xs[sel].contiguous(), Ts[sel].contiguous(), lr_ep, loss_out=loss)
+            net.train_step_rows(Xs, Ts, perm[s * batch:(s + 1) * batch], lr_ep, loss_out=loss)
             acc += loss.item() if (s % 16 == 0) else 0.0
         history.append(acc / max(1, (steps + 15) // 16))
         if log:

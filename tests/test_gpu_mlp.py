@@ -157,3 +157,23 @@ def test_trained_predictor_removes_steps_at_equal_error():
           f"E vs exact max {E['none'].max():.3g} -> {E['predicted'].max():.3g}")
     assert E["predicted"].max() <= max(10.0 * E["none"].max(), 30.0)
     assert np.median(E["predicted"]) <= max(3.0 * np.median(E["none"]), 1.0)
+
+
+def test_train_step_on_gathered_rows_matches_the_plain_step():
+    """kin_mlp_train_step_rows gathers a minibatch inside the library: on a
+    permutation's rows it must equal the plain step on those rows copied."""
+    rng = np.random.default_rng(3)
+    R, M, din, w, dout = 300, 64, 20, 32, 12
+    X = torch.from_numpy(rng.normal(size=(R, din)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(R, dout)).astype(np.float32)).cuda()
+    rows = torch.from_numpy(rng.permutation(R)[:M].astype(np.int32)).cuda()
+    a = kin.MLP(din, w, dout, precision="bf16", seed=5)
+    b = kin.MLP(din, w, dout, precision="bf16", seed=5)
+    la = torch.zeros(1, dtype=torch.float32, device="cuda")
+    lb = torch.zeros(1, dtype=torch.float32, device="cuda")
+    a.train_step_rows(X, T, rows, 1e-3, loss_out=la)
+    idx = rows.long()
+    b.train_step(X[idx].contiguous(), T[idx].contiguous(), 1e-3, loss_out=lb)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.get_params(), b.get_params())
+    assert la.item() == lb.item()

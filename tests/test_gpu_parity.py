@@ -163,6 +163,27 @@ def test_h2_1024_parity(layout, h2, h2_oracle):
     assert same.mean() >= 0.99, same.mean()
 
 
+def test_h2_1024_error_against_the_exact_solution(h2):
+    """|E| of Sec. 2.3 for the 1024-state H2 problem at dt = 1e-6 s: the
+    integrator's result against a tight-tolerance reference (oracle at rtol
+    1e-13, atol 1e-20, untransformed), weights atol 1e-10 / rtol 1e-6.  The
+    paper reports |E| of order one for its Radau IIA; the FP32 Newton
+    matrices must not change it materially."""
+    mech, mg, st = h2
+    Yx, Tx, _ = O.integrate(mech, st, 1e-6, rtol=1e-13, atol=1e-20, transform_tol=False)
+    yx = np.concatenate([Tx[None], Yx[:-1]])
+    out = {}
+    for f32 in (False, True):
+        Yg, Tg, cg, sg = run_gpu(mg, st, 1e-6, layout="plain", lu_fp32=f32)
+        assert np.all(sg == 0)
+        E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), yx)
+        out[f32] = (E.max(), np.median(E))
+    print(f"\n|E| FP64 matrices {out[False][0]:.3g} (median {out[False][1]:.3g}); "
+          f"FP32 {out[True][0]:.3g} (median {out[True][1]:.3g})")
+    assert out[False][0] < 30.0 and out[True][0] < 30.0
+    assert out[True][1] < 3.0 * out[False][1] + 1e-3
+
+
 def test_layouts_agree_bitwise(h2):
     mech, mg, st = h2
     a = run_gpu(mg, st, 1e-6, layout="plain")
