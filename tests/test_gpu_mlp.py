@@ -176,4 +176,5 @@ def test_train_step_on_gathered_rows_matches_the_plain_step():
     b.train_step(X[idx].contiguous(), T[idx].contiguous(), 1e-3, loss_out=lb)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(a.get_params(), b.get_params())
-    assert la.item() == lb.item()
+    # the loss is a sum of float atomics: equal up to its summation order
+    np.testing.assert_allclose(la.item(), lb.item(), rtol=1e-5)
