@@ -421,14 +421,17 @@ __device__ __forceinline__ int rhs(const MechView &m, double P, const double *y,
 }
 
 // ---------------------------------------------------------------------------
-// Dense LU with partial pivoting (row-major, leading dimension n).
+// Dense LU with partial pivoting (row-major, leading dimension n).  The loops
+// stay rolled (#pragma unroll 1) to keep the instruction footprint small.
 // Returns 0 or k+1 when column k has no nonzero pivot.
 // ---------------------------------------------------------------------------
 template <typename LT>
 __device__ __noinline__ int lu_real(int n, LT *a, int *ip) {
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     int p = k;
     LT amax = fabs(a[k * n + k]);
+    #pragma unroll 1
     for (int i = k + 1; i < n; ++i) {
       LT v = fabs(a[i * n + k]);
       if (v > amax) {
@@ -439,16 +442,19 @@ __device__ __noinline__ int lu_real(int n, LT *a, int *ip) {
     ip[k] = p;
     if (amax == LT(0)) return k + 1;
     if (p != k)
+      #pragma unroll 1
       for (int j = 0; j < n; ++j) {
         LT t = a[k * n + j];
         a[k * n + j] = a[p * n + j];
         a[p * n + j] = t;
       }
     const LT inv = LT(1) / a[k * n + k];
+    #pragma unroll 1
     for (int i = k + 1; i < n; ++i) {
       LT l = a[i * n + k] * inv;
       a[i * n + k] = l;
       if (l != LT(0))
+        #pragma unroll 1
         for (int j = k + 1; j < n; ++j) a[i * n + j] -= l * a[k * n + j];
     }
   }
@@ -460,7 +466,9 @@ __device__ __noinline__ int lu_real(int n, LT *a, int *ip) {
 template <int MAXN, typename LT, typename VT>
 __device__ __noinline__ void lu_solve_real(int n, const LT *lu, const int *ip, VT *b) {
   LT v[MAXN];
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) v[k] = LT(b[k]);
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     const int p = ip[k];
     if (p != k) {
@@ -469,16 +477,21 @@ __device__ __noinline__ void lu_solve_real(int n, const LT *lu, const int *ip, V
       v[p] = t;
     }
   }
+  #pragma unroll 1
   for (int i = 1; i < n; ++i) {
     LT s = v[i];
+    #pragma unroll 1
     for (int j = 0; j < i; ++j) s -= lu[i * n + j] * v[j];
     v[i] = s;
   }
+  #pragma unroll 1
   for (int i = n - 1; i >= 0; --i) {
     LT s = v[i];
+    #pragma unroll 1
     for (int j = i + 1; j < n; ++j) s -= lu[i * n + j] * v[j];
     v[i] = s / lu[i * n + i];
   }
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) b[k] = VT(v[k]);
 }
 
@@ -498,9 +511,11 @@ __device__ __forceinline__ void cdiv(LT a, LT b, LT c, LT d, LT &re, LT &im) {
 
 template <typename LT>
 __device__ __noinline__ int lu_cplx(int n, LT *ar, LT *ai, int *ip) {
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     int p = k;
     LT amax = fabs(ar[k * n + k]) + fabs(ai[k * n + k]);
+    #pragma unroll 1
     for (int i = k + 1; i < n; ++i) {
       LT v = fabs(ar[i * n + k]) + fabs(ai[i * n + k]);
       if (v > amax) {
@@ -511,6 +526,7 @@ __device__ __noinline__ int lu_cplx(int n, LT *ar, LT *ai, int *ip) {
     ip[k] = p;
     if (amax == LT(0)) return k + 1;
     if (p != k)
+      #pragma unroll 1
       for (int j = 0; j < n; ++j) {
         LT t = ar[k * n + j];
         ar[k * n + j] = ar[p * n + j];
@@ -520,12 +536,14 @@ __device__ __noinline__ int lu_cplx(int n, LT *ar, LT *ai, int *ip) {
         ai[p * n + j] = t;
       }
     const LT pr = ar[k * n + k], pi = ai[k * n + k];
+    #pragma unroll 1
     for (int i = k + 1; i < n; ++i) {
       LT lr, li;
       cdiv(ar[i * n + k], ai[i * n + k], pr, pi, lr, li);
       ar[i * n + k] = lr;
       ai[i * n + k] = li;
       if (lr != LT(0) || li != LT(0))
+        #pragma unroll 1
         for (int j = k + 1; j < n; ++j) {
           LT ur = ar[k * n + j], ui = ai[k * n + j];
           ar[i * n + j] -= lr * ur - li * ui;
@@ -540,10 +558,12 @@ template <int MAXN, typename LT, typename VT>
 __device__ __noinline__ void lu_solve_cplx(int n, const LT *lr, const LT *li, const int *ip, VT *br,
                                            VT *bi) {
   LT vr[MAXN], vi[MAXN];
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     vr[k] = LT(br[k]);
     vi[k] = LT(bi[k]);
   }
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     const int p = ip[k];
     if (p != k) {
@@ -555,8 +575,10 @@ __device__ __noinline__ void lu_solve_cplx(int n, const LT *lr, const LT *li, co
       vi[p] = t;
     }
   }
+  #pragma unroll 1
   for (int i = 1; i < n; ++i) {
     LT sr = vr[i], si = vi[i];
+    #pragma unroll 1
     for (int j = 0; j < i; ++j) {
       const LT xr = vr[j], xi = vi[j];
       sr -= lr[i * n + j] * xr - li[i * n + j] * xi;
@@ -565,8 +587,10 @@ __device__ __noinline__ void lu_solve_cplx(int n, const LT *lr, const LT *li, co
     vr[i] = sr;
     vi[i] = si;
   }
+  #pragma unroll 1
   for (int i = n - 1; i >= 0; --i) {
     LT sr = vr[i], si = vi[i];
+    #pragma unroll 1
     for (int j = i + 1; j < n; ++j) {
       const LT xr = vr[j], xi = vi[j];
       sr -= lr[i * n + j] * xr - li[i * n + j] * xi;
@@ -577,6 +601,7 @@ __device__ __noinline__ void lu_solve_cplx(int n, const LT *lr, const LT *li, co
     vr[i] = qr;
     vi[i] = qi;
   }
+  #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     br[k] = VT(vr[k]);
     bi[k] = VT(vi[k]);
