@@ -103,3 +103,33 @@ def test_order_states_validates_on_host():
                               None) == kin.KIN_ERR_INVALID_ARG
     o = kin.options()
     assert o.order is None
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/kin.h, from gcc."""
+    import subprocess
+    import tempfile
+    body = "\n".join(f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = f"""#include <stddef.h>
+#include <stdio.h>
+#include "kin.h"
+int main(void) {{
+  printf("%zu\\n", sizeof({struct}));
+{body}
+  return 0;
+}}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("ctype,cname", [(kin.Options, "kin_options"), (kin.MechDesc, "kin_mech_desc")])
+def test_binding_structs_match_the_header_layout(ctype, cname):
+    names = [f[0] for f in ctype._fields_]
+    size, offs = _c_layout(cname, names)
+    assert size == C.sizeof(ctype)
+    assert offs == [getattr(ctype, n).offset for n in names]
