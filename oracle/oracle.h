@@ -62,6 +62,7 @@ typedef struct {
   int32_t nstep, naccpt, nrejct, nfcn, njac, ndec, nsol, status;
   double h_first;      /* first accepted internal step */
   double h_last;       /* step size proposed after the last accepted step */
+  double err_last;     /* scaled error estimate of the last accepted step */
 } orc_stats;
 
 /* per-state status codes */

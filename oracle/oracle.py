@@ -60,7 +60,7 @@ class _Stats(C.Structure):
     _fields_ = [("nstep", C.c_int32), ("naccpt", C.c_int32), ("nrejct", C.c_int32),
                 ("nfcn", C.c_int32), ("njac", C.c_int32), ("ndec", C.c_int32),
                 ("nsol", C.c_int32), ("status", C.c_int32), ("h_first", C.c_double),
-                ("h_last", C.c_double)]
+                ("h_last", C.c_double), ("err_last", C.c_double)]
 
 
 class _Tableau(C.Structure):
@@ -262,7 +262,7 @@ def radau(f, jacobian, y0, t0, t1, **kw):
     if err:
         raise err[0]
     stats = {k: getattr(st, k) for k in ("nstep", "naccpt", "nrejct", "nfcn", "njac", "ndec",
-                                         "nsol", "status", "h_first", "h_last")}
+                                         "nsol", "status", "h_first", "h_last", "err_last")}
     return y, stats
 
 

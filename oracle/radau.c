@@ -440,6 +440,7 @@ int orc_radau(int n, orc_rhs_fn f, orc_jac_fn jac, void *ctx, double t0, double 
       /* accepted */
       first = 0;
       st->naccpt++;
+      st->err_last = err;
       if (!fixed) {
         if (st->naccpt > 1) {
           double facgus = (hacc / h) * pow(err * err / erracc, 0.25) / safe;

@@ -182,3 +182,21 @@ def test_final_step_below_round_off_of_t_ends_the_integration():
     y, st = O.radau(lambda t, v: lam * v, lambda t, v: np.array([[lam]]), [1.0],
                     1.0, 2.0, h0=1e-18)
     assert st["status"] == 2
+
+
+def test_error_estimate_scales_as_h_to_the_fourth():
+    """The embedded estimate (order-3 companion of the order-5 method) is a
+    local error of order h^4 on a smooth problem: its ratio per halving of a
+    constant step tends to 2^4.  Measured on the second of two steps, so the
+    first-step refinement does not enter."""
+    lam = -1.0
+    hs = [0.1, 0.05, 0.025, 0.0125]
+    errs = []
+    for h in hs:
+        y, st = O.radau(lambda t, v: lam * v, lambda t, v: np.array([[lam]]), [1.0], 0.0,
+                        2 * h, hfixed=h, rtol=1e-10, atol=1e-10, transform_tol=False)
+        assert st["status"] == 0 and st["naccpt"] == 2
+        errs.append(st["err_last"])
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(np.diff(ratios) > 0), ratios          # approaching the asymptote
+    assert 15.0 <= ratios[-1] <= 17.0, ratios
