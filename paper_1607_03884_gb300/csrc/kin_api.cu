@@ -569,24 +569,25 @@ extern "C" int kin_integrate_host(kin_mech *m, double *Y, double *T, const doubl
     }
     m->h_cap = n;
   }
-  if (n == 0) return kin_integrate_ex(m, m->h_Y, m->h_T, m->h_P, 0, dt, rtol, atol, opt, nullptr,
-                                      nullptr, stream);
-  KIN_CUDA_TRY(cudaMemcpyAsync(m->h_Y, Y, sizeof(double) * n * ns, cudaMemcpyHostToDevice, st));
-  KIN_CUDA_TRY(cudaMemcpyAsync(m->h_T, T, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  KIN_CUDA_TRY(cudaMemcpyAsync(m->h_P, P, sizeof(double) * n, cudaMemcpyHostToDevice, st));
   kin_options o;
   if (opt) {
     o = *opt;
   } else {
     kin_options_default(&o);
   }
-  if (o.order_by == 1) {  // stiffness ordering into the entry's own buffers
+  const bool order = o.order_by == 1;
+  o.order_by = 0;  // handled here; the device entry takes the explicit order
+  if (n == 0) return kin_integrate_ex(m, m->h_Y, m->h_T, m->h_P, 0, dt, rtol, atol, &o, nullptr,
+                                      nullptr, stream);
+  KIN_CUDA_TRY(cudaMemcpyAsync(m->h_Y, Y, sizeof(double) * n * ns, cudaMemcpyHostToDevice, st));
+  KIN_CUDA_TRY(cudaMemcpyAsync(m->h_T, T, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  KIN_CUDA_TRY(cudaMemcpyAsync(m->h_P, P, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if (order) {  // stiffness ordering into the entry's own buffers
     rc = kin_order_states(m, m->h_Y, m->h_T, m->h_P, n, rtol, atol, KIN_KEY_STEP_HEURISTIC,
                           m->h_key, m->h_order, stream);
     if (rc) return rc;
     o.order = m->h_order;
   }
-  o.order_by = 0;  // handled here; the device entry takes the explicit order
   rc = kin_integrate_ex(m, m->h_Y, m->h_T, m->h_P, n, dt, rtol, atol, &o,
                         status ? m->h_status : nullptr, counters ? m->h_cnt : nullptr, stream);
   if (rc) return rc;

@@ -481,6 +481,9 @@ def test_host_entry_matches_device_entry(h2):
     np.testing.assert_array_equal(cnt2.T, cd)
     with pytest.raises(kin.KinError):   # the device entry takes an explicit order
         run_gpu(mg, st, 1e-6, order_by="heuristic")
+    # an empty batch with ordering asked for is a no-op
+    mg.integrate_host(np.zeros((mech.ns, 0)), np.zeros(0), np.zeros(0), 1e-6,
+                      order_by="heuristic")
 
 
 def test_default_entry_is_queue_fp64(h2):
