@@ -3,11 +3,19 @@
 Workload: the seeded H2/O2-like mechanism (13 species, 27 reactions) on 2^20
 PaSR-like states (20 % near-equilibrium products, 80 % ignition-delay
 states, random order), one global step dt (default 1e-4 s; 1e-6 s is also
-reported), rtol 1e-6, atol 1e-10.  A step is one kin_integrate of the whole
-batch; inputs are restored from a pristine device copy and L2 is flushed
-(256 MiB write) before every timed step, outside the timed region.
+reported), rtol 1e-6, atol 1e-10.  The launch configuration is autotuned
+(kin_autotune on a 2^18-state prefix).  A timed step is one replay of a CUDA
+graph holding the stiffness ordering (kin_order_states) and one integration
+of the whole batch; inputs are restored from a pristine device copy and L2
+is flushed (256 MiB write) before every timed step, outside the timed
+region.  After the timed steps it measures, untimed for the headline: the
+plain FP64 one-state-per-thread kernel on the same states and the error
+between the two, the other dt, the warp divergence D, the same integration
+through the host-buffer entry (copies included), and the oracle on a
+sample of the states on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload ch4_2p18 --layout warp ...   (other workloads)
 
 Under torchrun each rank integrates its own copy of the workload (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
