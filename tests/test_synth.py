@@ -48,3 +48,31 @@ def test_states_recipe(h2_mech):
     eb = h2_mech.comp.T.astype(float) @ (yb / h2_mech.W)
     np.testing.assert_allclose(el, eb, rtol=1e-12)
     assert abs(el[0] / el[1] - 2.0) < 1e-12
+
+
+@pytest.mark.parametrize("name,kind,n,seed", [
+    ("h2_1024", "h2", 1024, 42), ("h2_mixed_2p20", "h2", 1 << 20, 43),
+    ("ch4_2p18", "ch4", 1 << 18, 44), ("ch4_2p16", "ch4", 1 << 16, 45),
+    ("ch4_learned_test_2p20", "ch4", 1 << 20, 46), ("ch4_learned_train_2p20", "ch4", 1 << 20, 47)])
+def test_workload_registry(name, kind, n, seed):
+    w = synth.WORKLOADS[name]
+    assert (w["kind"], w["n"], w["seed"]) == (kind, n, seed)
+    if n <= 1 << 16:   # a prefix is the first states of the full batch
+        mech, full, _ = synth.workload(name)
+        _, pre, _ = synth.workload(name, 16)
+        np.testing.assert_array_equal(pre.T, full.T[:16])
+        np.testing.assert_array_equal(pre.Y, full.Y[:, :16])
+
+
+@pytest.mark.parametrize("kind", ["h2", "ch4"])
+def test_thermo_fits_are_monotone_in_range(kind, h2_mech, ch4_mech):
+    """cp/R of every species is monotone in T and within [2.5, 6] over
+    300-3000 K, with the same coefficients in both NASA-7 ranges."""
+    m = h2_mech if kind == "h2" else ch4_mech
+    T = np.linspace(300.0, 3000.0, 271)
+    for k in range(m.ns):
+        lo, hi = m.nasa[k, 3:10], m.nasa[k, 10:17]
+        np.testing.assert_array_equal(lo, hi)
+        cp = lo[0] + T * (lo[1] + T * (lo[2] + T * (lo[3] + T * lo[4])))
+        assert np.all(np.diff(cp) >= -1e-12), k
+        assert cp.min() >= 2.5 - 1e-9 and cp.max() <= 6.0 + 1e-9, (k, cp.min(), cp.max())
