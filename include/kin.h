@@ -54,7 +54,8 @@ typedef enum {
 enum {
   KIN_STATE_OK = 0,
   KIN_STATE_MAX_STEPS = 1,   /* internal step limit reached */
-  KIN_STATE_H_UNDERFLOW = 2, /* internal step below round-off of t */
+  KIN_STATE_H_UNDERFLOW = 2, /* internal step below round-off of t (a final step
+                                that short instead ends the integration at dt) */
   KIN_STATE_SINGULAR = 3,    /* iteration matrix singular 5 times in a row */
   KIN_STATE_NONFINITE = 4,   /* non-finite right-hand side or Jacobian */
   KIN_STATE_NEWTON_FIXED = 5 /* kin_options.h_fixed: Newton failed at the fixed step */
