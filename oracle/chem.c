@@ -350,29 +350,22 @@ int orc_jac(const orc_mech *m, double P, const double *y, double *J) {
   return ok ? 0 : ORC_NONFINITE;
 }
 
-/* One-sided difference-quotient Jacobian "based on that of CVODE" (Sec. 2.1):
- * column j uses the increment max(sqrt(eps)|y_j|, minInc / w_j) with
- * w_j = 1/scal_j the error weights and minInc = 1000 |h| eps N ||f||_w
- * (1 when ||f||_w = 0), ||.||_w the weighted RMS norm. */
+/* The chemistry's difference-quotient Jacobian: the generic one-sided rule
+ * of orc_fd_jacobian (radau.c, "based on that of CVODE", Sec. 2.1) applied to
+ * orc_rhs at fixed pressure. */
+typedef struct {
+  const orc_mech *m;
+  double P;
+} fd_ctx;
+
+static int fd_rhs(void *c, double t, const double *y, double *f) {
+  (void)t;
+  const fd_ctx *k = (const fd_ctx *)c;
+  return orc_rhs(k->m, k->P, y, f);
+}
+
 int orc_jac_fd(const orc_mech *m, double P, const double *y, const double *f0, double h,
                const double *scal, double *J) {
-  int N = m->ns;
-  const double uround = DBL_EPSILON;
-  double *yy = malloc(sizeof(double) * 2 * N), *ft = yy + N;
-  double fn = 0.0;
-  for (int i = 0; i < N; ++i) fn += (f0[i] / scal[i]) * (f0[i] / scal[i]);
-  fn = sqrt(fn / N);
-  double minInc = (fn != 0.0) ? 1000.0 * fabs(h) * uround * N * fn : 1.0;
-  memcpy(yy, y, sizeof(double) * N);
-  int rc = 0;
-  for (int j = 0; j < N; ++j) {
-    double inc = fmax(sqrt(uround) * fabs(y[j]), minInc * scal[j]);
-    yy[j] = y[j] + inc;
-    int r = orc_rhs(m, P, yy, ft);
-    if (r) rc = r;
-    for (int i = 0; i < N; ++i) J[(size_t)i * N + j] = (ft[i] - f0[i]) / inc;
-    yy[j] = y[j];
-  }
-  free(yy);
-  return rc;
+  fd_ctx c = {m, P};
+  return orc_fd_jacobian(m->ns, fd_rhs, &c, 0.0, y, f0, h, scal, J);
 }

@@ -106,6 +106,8 @@ int orc_radau(int n, orc_rhs_fn f, orc_jac_fn jac, void *ctx, double t0, double 
               double *y, const orc_opts *o, orc_stats *st);
 double orc_initial_step(int n, orc_rhs_fn f, void *ctx, double t0, double t1,
                         const double *y, const double *f0, double rtol, double atol, int *nfcn);
+int orc_fd_jacobian(int n, orc_rhs_fn f, void *ctx, double t, const double *y, const double *f0,
+                    double h, const double *scal, double *J);
 
 /* batch.c */
 int orc_integrate_batch(const orc_mech *m, int64_t n, double *Y, double *T, const double *P,

@@ -96,6 +96,9 @@ def lib():
             L.orc_lu_solve_cplx.argtypes = [i, vp, vp, vp]
             L.orc_radau_tableau.argtypes = [vp]
             L.orc_radau.argtypes = [i, RHS_FN, JAC_FN, vp, d, d, vp, vp, vp]
+            L.orc_initial_step.argtypes = [i, RHS_FN, vp, d, d, vp, vp, d, d, vp]
+            L.orc_initial_step.restype = d
+            L.orc_fd_jacobian.argtypes = [i, RHS_FN, vp, d, vp, vp, d, vp, vp]
             L.orc_integrate_batch.argtypes = [vp, C.c_int64, vp, vp, vp, d, vp, vp, vp, i]
             L.orc_num_threads.restype = i
             _lib = L
@@ -221,6 +224,54 @@ def make_opts(rtol=1e-6, atol=1e-10, transform_tol=True, nit=7, h0=0.0, hfixed=0
               None if z0 is None else _p(z0).value,
               None if z_first_out is None else _p(z_first_out).value)
     return o
+
+
+def _rhs_callback(f, n, err):
+    """A C right-hand-side callback around f(t, y) -> array."""
+    def _f(ctx, t, yp, fp):
+        try:
+            v = np.asarray(f(t, np.ctypeslib.as_array(yp, (n,)).copy()), dtype=np.float64)
+            if not np.all(np.isfinite(v)):
+                return 4
+            np.ctypeslib.as_array(fp, (n,))[:] = v
+            return 0
+        except Exception as e:  # pragma: no cover - surfaced by the caller
+            err.append(e)
+            return 4
+    return RHS_FN(_f)
+
+
+def initial_step(f, y0, t0, t1, rtol, atol):
+    """The oracle's starting-step heuristic (orc_initial_step) for y' = f(t, y)
+    at (t0, y0), with the tolerances given as they enter the weights
+    atol + rtol |y| (no transform).  Returns (h, right-hand sides used)."""
+    n = len(y0)
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    err = []
+    cf = _rhs_callback(f, n, err)
+    f0 = np.ascontiguousarray(f(t0, y.copy()), dtype=np.float64)
+    nf = C.c_int(0)
+    h = lib().orc_initial_step(n, cf, None, float(t0), float(t1), _p(y), _p(f0), float(rtol),
+                               float(atol), C.byref(nf))
+    if err:
+        raise err[0]
+    return float(h), int(nf.value)
+
+
+def fd_jacobian(f, y, h, scal, t=0.0):
+    """The oracle's one-sided difference-quotient Jacobian (orc_fd_jacobian) of a
+    generic f(t, y) at y with the internal step h and error weights scal."""
+    n = len(y)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    scal = np.ascontiguousarray(scal, dtype=np.float64)
+    err = []
+    cf = _rhs_callback(f, n, err)
+    f0 = np.ascontiguousarray(f(t, y.copy()), dtype=np.float64)
+    J = np.zeros((n, n))
+    rc = lib().orc_fd_jacobian(n, cf, None, float(t), _p(y), _p(f0), float(h), _p(scal), _p(J))
+    if err:
+        raise err[0]
+    return J, rc
 
 
 def radau(f, jacobian, y0, t0, t1, **kw):

@@ -181,6 +181,35 @@ double orc_initial_step(int n, orc_rhs_fn f, void *ctx, double t0, double t1, co
   return fmin(h, t1 - t0);
 }
 
+/* One-sided difference-quotient Jacobian "based on that of CVODE" (Sec. 2.1,
+ * Sec. 3.4) of a generic right-hand side: column j is
+ * (f(t, y + inc_j e_j) - f0) / inc_j with the increment
+ * inc_j = max(sqrt(eps)|y_j|, minInc scal_j), scal_j = 1/w_j the error
+ * weights and minInc = 1000 |h| eps n ||f0||_w (1 when ||f0||_w = 0),
+ * ||.||_w the weighted RMS norm.  J is row-major, J[i*n + j] = df_i/dy_j.
+ * Returns the last nonzero status of f, else 0. */
+int orc_fd_jacobian(int n, orc_rhs_fn f, void *ctx, double t, const double *y, const double *f0,
+                    double h, const double *scal, double *J) {
+  const double uround = DBL_EPSILON;
+  double *yy = malloc(sizeof(double) * 2 * n), *ft = yy + n;
+  double fn = 0.0;
+  for (int i = 0; i < n; ++i) fn += (f0[i] / scal[i]) * (f0[i] / scal[i]);
+  fn = sqrt(fn / n);
+  double minInc = (fn != 0.0) ? 1000.0 * fabs(h) * uround * n * fn : 1.0;
+  memcpy(yy, y, sizeof(double) * n);
+  int rc = 0;
+  for (int j = 0; j < n; ++j) {
+    double inc = fmax(sqrt(uround) * fabs(y[j]), minInc * scal[j]);
+    yy[j] = y[j] + inc;
+    int r = f(ctx, t, yy, ft);
+    if (r) rc = r;
+    for (int i = 0; i < n; ++i) J[(size_t)i * n + j] = (ft[i] - f0[i]) / inc;
+    yy[j] = y[j];
+  }
+  free(yy);
+  return rc;
+}
+
 enum { NEED_JAC = 2, NEED_LU = 1, NEED_NONE = 0 };
 
 int orc_radau(int n, orc_rhs_fn f, orc_jac_fn jac, void *ctx, double t0, double t1, double *y,
