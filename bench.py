@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--fp32", type=int, default=1, help="FP32 Newton matrices (1) or FP64 (0)")
     p.add_argument("--n", type=int, default=0, help="states (0 = the workload's 2^20)")
     p.add_argument("--no-extras", action="store_true", help="skip the comparison legs")
+    p.add_argument("--no-config3", action="store_true",
+                   help="skip the full-size CH4-like leg among the extras")
     p.add_argument("--cpu-sample", type=int, default=2048)
     p.add_argument("--order", default="heuristic", choices=["none", "heuristic"],
                    help="order the states by the starting-step heuristic inside each step")
@@ -70,28 +72,33 @@ def parse():
 # ---------------------------------------------------------------------------
 
 def op_model(mech):
-    """Flops of one right-hand side, Jacobian, factorisation pair and Newton
-    solve pair for this mechanism (transcendentals count as one flop)."""
-    ns, N = mech.ns, mech.ns
-    neff = [(int(np.sum(mech.eff[i] != 1.0)) if mech.rtype[i] else 0) for i in range(mech.nr)]
-    slots = [int(np.sum(mech.reac[i] >= 0) + np.sum(mech.prod[i] >= 0)) for i in range(mech.nr)]
-    f_rhs = 36 * ns + 3 * N
-    for i in range(mech.nr):
-        f_rhs += 20 + 2 * slots[i] + 2 * neff[i] + (45 if mech.rtype[i] == 2 else 0)
-    f_jac = f_rhs + 10 * N * N
-    for i in range(mech.nr):
-        f_jac += 12 + slots[i] * (4 * slots[i] + 4 * neff[i]) + (30 if mech.rtype[i] == 2 else 0)
-    f_lu = (2.0 / 3.0) * N ** 3 + (8.0 / 3.0) * N ** 3 + 3 * N * N   # real + complex + build
-    f_sol = 2 * N * N + 8 * N * N + 40 * N                           # both solves + transforms
-    f_err = 2 * N * N + 10 * N
-    return dict(rhs=f_rhs, jac=f_jac, lu=f_lu, sol=f_sol, err=f_err)
+    """Counted operations per event for this mechanism (oracle/flop_counts.json,
+    written by oracle/opcount.py; transcendentals count as one operation), or
+    None when the mechanism has no committed count."""
+    from oracle import opcount
+    rec = opcount.load_counts(mech)
+    return None if rec is None else opcount.per_event(rec)
 
 
 def algorithmic_flops(tot, ops, fp32):
-    """FP64 and FP32 flops of one launch from the summed counters."""
-    f64 = tot["nfcn"] * ops["rhs"] + tot["njac"] * ops["jac"] + tot["naccpt"] * ops["err"]
-    lin = tot["ndec"] * ops["lu"] + tot["nsol"] * ops["sol"]
-    return (f64, lin) if fp32 else (f64 + lin, 0.0)
+    """(FP64, FP32) operations of one launch from its summed counters.
+
+    Events: right-hand sides (nfcn), Jacobians beyond their point's f (njac),
+    factorisation pairs (ndec), Newton iterations (nsol: both solves and the
+    iteration's algebra), error estimates (at least naccpt + nrejct: every
+    accepted step and every error-test rejection after the first acceptance;
+    the uncounted ones make this a lower bound), step attempts (nstep) and
+    accepted steps (naccpt).  With FP32 Newton matrices the factorisations,
+    the solves and the Jacobian assembly are FP32 work."""
+    nerr = tot["naccpt"] + tot["nrejct"]
+    lin = tot["ndec"] * ops["lu_linear"] + tot["nsol"] * ops["sol_linear"] + nerr * ops["err_linear"]
+    jac = tot["njac"] * ops["jac"]
+    total = (tot["nfcn"] * ops["rhs"] + jac + tot["ndec"] * ops["lu"] + tot["nsol"] * ops["sol"]
+             + nerr * ops["err"] + tot["nstep"] * ops["step"] + tot["naccpt"] * ops["accept"])
+    if not fp32:
+        return float(total), 0.0
+    f32 = lin + jac
+    return float(total - f32), float(f32)
 
 
 # ---------------------------------------------------------------------------
@@ -252,7 +259,7 @@ def run_ours(args, rank, world):
     t_median = float(np.median(times))
     t_max = max_over_ranks(t_step, dist, "cuda")
     value = whole_job_rate(n, world, t_max)
-    f64, f32 = algorithmic_flops(tot, ops, bool(args.fp32))
+    f64, f32 = algorithmic_flops(tot, ops, bool(args.fp32)) if ops else (None, None)
 
     out = {"tune": tune, "opt": {k: v for k, v in opt.items()}}
     if rank == 0 and not args.no_extras:
@@ -315,12 +322,51 @@ def run_ours(args, rank, world):
         out["e2e"] = {"value": n / float(np.mean(te)), "unit": "states/s",
                       "h2d_bytes_per_step": int(n * (mech.ns + 2) * 8),
                       "d2h_bytes_per_step": int(n * (mech.ns + 1) * 8)}
+    if rank == 0 and not args.no_extras and not args.no_config3 and args.workload == WORKLOAD:
+        out["configs"] = {"ch4_2p18": config3_leg(stream)}
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return dict(value=value, t_step=t_max, t_median=t_median, times=times, wall=wall,
                 clocks=clocks, tot=tot,
                 f64=f64, f32=f32, n=n, mech=mech, st=st, extras=out)
+
+
+def config3_leg(stream):
+    """The CH4-like configuration at full size, outside the headline's timed
+    region: 2^18 states (53 species, 325 reactions), dt = 1e-4 s, the state-
+    per-warp layout with FP32 Newton matrices.  One warm-up launch on a 4096-
+    state prefix, then one timed launch of the whole batch (CUDA events on the
+    launching stream, L2 flushed before), with its own counted roofline."""
+    import torch
+    from paper_1607_03884_gb300 import kin, synth
+    mech, st, _ = synth.workload("ch4_2p18")
+    mg = kin.Mechanism(mech)
+    opt = dict(layout="warp", lanes=32, lu_fp32=True)
+    Y, T, P = (torch.from_numpy(a.copy()).cuda() for a in (st.Y, st.T, st.P))
+    m = 4096
+    mg.integrate(Y[:, :m].contiguous(), T[:m].clone(), P[:m].contiguous(), 1e-4, RTOL, ATOL,
+                 stream=stream, **opt)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush.zero_()
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mg.integrate(Y, T, P, 1e-4, RTOL, ATOL, stream=stream, **opt)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = clk.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    tot = mg.stats()
+    ops = op_model(mech)
+    f64, f32 = algorithmic_flops(tot, ops, True) if ops else (None, None)
+    return {"workload": "ch4_2p18", "states": st.n, "species": mech.ns, "reactions": mech.nr,
+            "dt": 1e-4, "layout": "warp", "lanes": 32, "newton_matrices": "fp32",
+            "value": st.n / sec, "unit": "states/s", "seconds": sec, "failed": tot["failed"],
+            "counters": {k: int(v) for k, v in tot.items()}, "clocks": clocks,
+            "roofline": roofline(f64, f32, sec, None, "k_integrate_lanes<32, float>")}
 
 
 def cpu_model():
@@ -397,11 +443,30 @@ def peaks():
         return {}
 
 
-# FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock).
-# The unit count is measured on this GB300 (dependent-FMA kernel on all SMs:
-# 1.198 TFLOP/s); FP32: 152 x 128 lanes x 2 x 2.07 GHz.
+# FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock);
+# the unit count was measured on this GB300, and a dependent-FMA kernel on all
+# SMs reached FP64_PROBE_TFLOPS.  FP32: 152 x 128 lanes x 2 x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PROBE_TFLOPS = 1.198
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def roofline(f64, f32, seconds, traffic=None, kernel=None):
+    """The FP64-pipe roofline of one launch from its counted operations."""
+    if f64 is None:
+        return {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": traffic, "note": "no committed operation count"}
+    a64 = f64 / seconds / 1e12
+    return {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": a64 / FP64_PEAK_TFLOPS, "traffic": traffic, "pipe": "fp64", "kernel": kernel,
+            "peak_source": "152 SMs x 2 FP64 FMA/clk x 2.07 GHz (unit count measured)",
+            "frac_of_probe_peak": a64 / FP64_PROBE_TFLOPS, "probe_peak": FP64_PROBE_TFLOPS,
+            "fp32_tflops": f32 / seconds / 1e12,
+            "time_bound_frac": a64 / FP64_PEAK_TFLOPS + f32 / seconds / 1e12 / FP32_PEAK_TFLOPS,
+            "flops_source": "operations per event counted by oracle/opcount.py "
+                            "(oracle/flop_counts.json) times the launch's event counters",
+            "traffic_source": "ncu dram__bytes_read+write of a 131072-state capture "
+                              "(profiles/dram_traffic.json), scaled by states"}
 
 
 def main():
@@ -433,16 +498,11 @@ def main():
     r = run_ours(args, rank, world)
     if rank != 0:
         return
-    pk = peaks()
     t = r["t_step"]
-    a64 = r["f64"] / t / 1e12
-    roof = {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": a64 / FP64_PEAK_TFLOPS,
-            "traffic": dram_traffic(f"{r['extras']['opt'].get('layout')}:"
-                                    f"{'f32' if args.fp32 else 'f64'}", r["n"]),
-            "pipe": "fp64", "kernel": f"k_integrate_{r['extras']['opt'].get('layout')}",
-            "peak_source": "152 SMs x 2 FP64 FMA/clk x 2.07 GHz (unit count measured)",
-            "fp32_tflops": r["f32"] / t / 1e12}
+    roof = roofline(r["f64"], r["f32"], t,
+                    dram_traffic(f"{r['extras']['opt'].get('layout')}:"
+                                 f"{'f32' if args.fp32 else 'f64'}", r["n"]),
+                    f"k_integrate_{r['extras']['opt'].get('layout')}")
     cb = cpu_baseline(args.cpu_sample, args.dt, args.workload) if not args.no_extras else None
     ex = r["extras"]
     line = {
@@ -473,6 +533,7 @@ def main():
         "error_vs_plain_fp64": ex.get("error_vs_plain_fp64"),
         "per_dt": ex.get("per_dt"),
         "divergence": ex.get("divergence"),
+        "configs": ex.get("configs"),
         "counters": {k: int(v) for k, v in r["tot"].items()},
     }
     print(json.dumps(line))
