@@ -99,18 +99,27 @@ enum {
                            whose state is done takes the next one from an
                            atomic work queue (answers the warp divergence of
                            Sec. 3.3: no lane waits for the slowest state) */,
-  KIN_LAYOUT_WARP = 2   /* one state per group of kin_options.lanes lanes
+  KIN_LAYOUT_WARP = 2,  /* one state per group of kin_options.lanes lanes
                            (a whole warp: ns <= 63; 4, 8 or 16 lanes:
                            ns <= 15): vectors over the group's lanes, Newton
                            matrices in shared memory, group-cooperative LU
                            and solves, rates in parallel over reactions;
                            groups pop states from the atomic queue (the
                            per-block strategy of Sec. 3.3) */
+  KIN_LAYOUT_AUTO = 3   /* the library chooses at each call: the launch
+                           configuration kin_autotune last found for this
+                           mechanism with the same matrix precision, Jacobian
+                           kind and decade of dt (of the tuned batch sizes,
+                           the one nearest to n in log2), else PLAIN with 64
+                           threads for ns <= 16 and WARP with 32 lanes beyond
+                           (the per-thread matrices no longer fit on chip);
+                           with h_fixed > 0, where WARP is not available,
+                           PLAIN.  kin_resolve_options shows the choice. */
 };
 
 /* Integration options.  kin_options_default fills the defaults. */
 typedef struct {
-  int32_t layout;        /* KIN_LAYOUT_*                                   (1) */
+  int32_t layout;        /* KIN_LAYOUT_*                                   (3) */
   int32_t lu_fp32;       /* 1: Jacobian storage, factorisation and solves of
                             the Newton matrices in FP32 (rates, residuals,
                             stage update, error estimate stay FP64)       (0) */
@@ -208,7 +217,10 @@ int kin_integrate_host(kin_mech *m, double *Y, double *T, const double *P, int64
 
 /* Autotuner: time candidate launch configurations on the caller's states
  * (Y, T, P dev, n states; copied, the inputs are not modified) and return the
- * fastest in *best.  Candidates for ns <= 15: PLAIN with 64 and 32 threads
+ * fastest in *best.  The result is also kept in the mechanism's tuning cache
+ * (keyed on the matrix precision, the Jacobian kind, the decade of dt and
+ * log2 n; at most 64 entries, a repeated key replaced), which
+ * KIN_LAYOUT_AUTO consults.  Candidates for ns <= 15: PLAIN with 64 and 32 threads
  * per block; QUEUE with 64 threads and refill batches 1, 4, 8, 16, 32; QUEUE
  * with 32 threads and refill 1; WARP with 32, 16, 8 and 4 lanes per state
  * (12 in all; the first max_candidates are timed).  ns = 16 drops the
@@ -225,6 +237,14 @@ int kin_integrate_host(kin_mech *m, double *Y, double *T, const double *P, int64
 int kin_autotune(kin_mech *m, const double *Y, const double *T, const double *P, int64_t n,
                  double dt, double rtol, double atol, const kin_options *base, kin_options *best,
                  double *seconds, int32_t max_candidates, void *stream);
+
+/* The launch configuration kin_integrate_ex would use for a batch of n
+ * states over dt with the options opt (NULL = defaults): *out = opt with
+ * KIN_LAYOUT_AUTO replaced by the chosen layout, block, queue_refill and
+ * lanes (other layouts are returned unchanged).  Host only; runs nothing on
+ * the GPU.  Errors: KIN_ERR_INVALID_ARG for NULL m or out, n < 0, dt <= 0. */
+int kin_resolve_options(kin_mech *m, int64_t n, double dt, const kin_options *opt,
+                        kin_options *out);
 
 /* Totals of the last kin_integrate* call on this mechanism, reduced on the
  * device: out[0..6] = sums of the KIN_CNT_* counters 0..6, out[7] = number of
@@ -276,16 +296,37 @@ int kin_jacobian(kin_mech *m, const double *y, const double *P, int64_t n, int32
 #define KIN_STATIC_SCRATCH_BYTES (64 * 1024 + 256)
 
 /* kin_integrate with the default options for callers that cannot allocate
- * device memory (no cudaMalloc, cudaFree or allocating library call is made):
- * the mechanism is passed as its host description and its tables, with the
- * kernel's counters, go to a fixed device array inside libkin
- * (KIN_STATIC_SCRATCH_BYTES) instead of a kin_mech's workspace.  The paper
- * has no counterpart; it exists for hosts whose allocator owns the device
- * memory.  Y, T, P and status are as for kin_integrate_ex (dev pointers).
- * The first call on a device looks up the array's device address; make it
- * before any stream capture.  Calls share the array: calls whose GPU work
- * overlaps race and must not be issued.  Errors: as kin_integrate, plus
- * KIN_ERR_UNSUPPORTED when the mechanism's tables exceed 64 KiB. */
+ * device memory: no cudaMalloc, cudaFree or allocating library call is made.
+ * Such callers run inside a host framework whose own allocator owns (and may
+ * have reserved) all device memory, or in a loop that must not allocate once
+ * running.  The mechanism is passed as its host description; its tables and
+ * the kernel's counters go to a fixed device array inside libkin
+ * (KIN_STATIC_SCRATCH_BYTES, held by every GPU that loads the library until
+ * the process exits) instead of a kin_mech's workspace.  The paper has no
+ * counterpart.  Y, T, P and status are as for kin_integrate_ex (dev
+ * pointers).
+ *   - Kernel: one state per thread (PLAIN), FP64 Newton matrices, whatever
+ *     the mechanism size: the state-per-warp layout needs a per-mechanism
+ *     workspace.  It serves mechanisms of up to 16 species at the thread
+ *     layouts' speed; larger ones are integrated correctly but far more
+ *     slowly than kin_integrate_ex would (its 64-species per-thread kernel).
+ *   - Set-up: the first call on a device looks up the array's device
+ *     address.  The first launch of an integration kernel on a device can
+ *     also make the CUDA driver reserve local memory for the kernel's
+ *     per-thread frame times the device's resident threads (gigabytes for
+ *     these kernels); a host whose allocator reserves all device memory
+ *     should make one call, on any small batch, before it does.
+ *   - Not capturable: the tables are uploaded from host memory the call
+ *     frees, so a call on a stream that is being captured into a CUDA graph
+ *     returns KIN_ERR_UNSUPPORTED and issues nothing.
+ *   - Sharing: every call uses the same array, rewrites the tables and
+ *     clears the counters before its launch; calls whose GPU work overlaps
+ *     (on different streams) race on it and must not be issued.  The
+ *     per-state status is the only diagnostic: kin_get_stats cannot see a
+ *     static call's totals, and the array's contents after a call are
+ *     unspecified.
+ * Errors: as kin_integrate, plus KIN_ERR_UNSUPPORTED when the mechanism's
+ * tables exceed 64 KiB or the stream is capturing. */
 int kin_integrate_static(const kin_mech_desc *desc, double *Y, double *T, const double *P,
                          int64_t n, double dt, double rtol, double atol, int32_t *status,
                          void *stream);

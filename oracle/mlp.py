@@ -34,15 +34,22 @@ def init(sizes, seed=0):
     return W, b
 
 
-def forward(W, b, x):
-    """Returns (y, cache) with pre-activations a_l and activations h_l."""
-    h = [np.asarray(x, dtype=np.float64)]
+def forward(W, b, x, rnd=None):
+    """Returns (y, cache) with pre-activations a_l and activations h_l.
+
+    rnd (optional) rounds every matrix the forward products read: the input
+    and each hidden activation before it enters the next layer (a
+    reduced-precision network that stores its activations at that
+    precision; the caller rounds the weights).  The arithmetic stays FP64
+    and the output is not rounded."""
+    r = (lambda v: v) if rnd is None else rnd
+    h = [r(np.asarray(x, dtype=np.float64))]
     a = []
     L = len(W)
     for l in range(L):
         z = h[-1] @ W[l] + b[l]
         a.append(z)
-        h.append(silu(z) if l < L - 1 else z)
+        h.append(r(silu(z)) if l < L - 1 else z)
     return h[-1], (h, a)
 
 
@@ -51,8 +58,13 @@ def loss(y, t):
     return float(np.mean(d * d))
 
 
-def backward(W, b, cache, y, t):
-    """Gradients of the MSE loss w.r.t. every W[l], b[l]."""
+def backward(W, b, cache, y, t, rnd=None):
+    """Gradients of the MSE loss w.r.t. every W[l], b[l].
+
+    rnd (optional) rounds the back-propagated gradient where the products
+    read it (the weight gradient and the gradient of the layer input); the
+    bias gradient sums it unrounded."""
+    r = (lambda v: v) if rnd is None else rnd
     h, a = cache
     L = len(W)
     g = 2.0 * (y - t) / y.size
@@ -60,9 +72,10 @@ def backward(W, b, cache, y, t):
     for l in range(L - 1, -1, -1):
         if l < L - 1:
             g = g * silu_grad(a[l])
-        gW[l] = h[l].T @ g
+        gr = r(g)
+        gW[l] = h[l].T @ gr
         gb[l] = g.sum(axis=0)
-        g = g @ W[l].T
+        g = gr @ W[l].T
     return gW, gb
 
 

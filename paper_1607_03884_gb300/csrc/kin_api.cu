@@ -24,8 +24,16 @@
 
 using namespace kin;
 
+// One tuned launch configuration (kin_autotune) and the key it answers.
+struct TuneEntry {
+  int lu_fp32, jac_fd, dt_decade, n_log2;
+  int layout, block, refill, lanes;
+};
+
 struct kin_mech {
   int device;
+  std::mutex tune_mu;
+  std::vector<TuneEntry> tuned;            // at most kMaxTuned entries
   MechLayout L;
   double *d_tab = nullptr;
   int *d_itab = nullptr;
@@ -195,7 +203,7 @@ __global__ void k_exp(const double *tab, const double *x, double *y, int64_t n) 
 extern "C" int kin_options_default(kin_options *o) {
   if (!o) return KIN_ERR_INVALID_ARG;
   std::memset(o, 0, sizeof *o);
-  o->layout = KIN_LAYOUT_QUEUE;
+  o->layout = KIN_LAYOUT_AUTO;
   o->lu_fp32 = 0;
   o->jac_fd = 0;
   o->max_steps = 100000;
@@ -462,6 +470,76 @@ int kin::launch_dispatch(const KernelArgs &a, const kin_options &o, cudaStream_t
   return o.lu_fp32 ? kin_launch_64f(a, o, st, sms) : kin_launch_64d(a, o, st, sms);
 }
 
+static constexpr size_t kMaxTuned = 64;
+
+static int dt_decade(double dt) { return (int)std::floor(std::log10(dt)); }
+static int n_log2(int64_t n) {
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << (b + 1)) <= n) ++b;
+  return b;
+}
+
+// KIN_LAYOUT_AUTO: the tuning cache's entry for (precision, Jacobian, dt
+// decade) nearest in log2 n, else the size rule (PLAIN up to 16 species,
+// WARP beyond; PLAIN at a fixed step, where WARP is not available).
+static void resolve_auto(kin_mech *m, int64_t n, double dt, kin_options &o) {
+  if (o.layout != KIN_LAYOUT_AUTO) return;
+  const int dd = dt_decade(dt), nb = n_log2(n > 0 ? n : 1);
+  const TuneEntry *best = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(m->tune_mu);
+    for (const TuneEntry &e : m->tuned) {
+      if (e.lu_fp32 != (o.lu_fp32 != 0) || e.jac_fd != (o.jac_fd != 0) || e.dt_decade != dd)
+        continue;
+      if (!best || std::abs(e.n_log2 - nb) < std::abs(best->n_log2 - nb)) best = &e;
+    }
+    if (best && !(o.h_fixed > 0.0 && best->layout == KIN_LAYOUT_WARP)) {
+      o.layout = best->layout;
+      o.block = best->block;
+      o.queue_refill = best->refill;
+      o.lanes = best->lanes;
+      return;
+    }
+  }
+  if (m->L.ns <= SMALL_MAXN || o.h_fixed > 0.0) {
+    o.layout = KIN_LAYOUT_PLAIN;
+    o.block = 64;
+    o.lanes = 0;
+  } else {
+    o.layout = KIN_LAYOUT_WARP;
+    o.block = 0;
+    o.lanes = 32;
+  }
+}
+
+static void remember_tuning(kin_mech *m, int64_t n, double dt, const kin_options &best) {
+  TuneEntry e{best.lu_fp32 != 0, best.jac_fd != 0, dt_decade(dt), n_log2(n),
+              best.layout, best.block, best.queue_refill, best.lanes};
+  std::lock_guard<std::mutex> lk(m->tune_mu);
+  for (TuneEntry &x : m->tuned)
+    if (x.lu_fp32 == e.lu_fp32 && x.jac_fd == e.jac_fd && x.dt_decade == e.dt_decade &&
+        x.n_log2 == e.n_log2) {
+      x = e;
+      return;
+    }
+  if (m->tuned.size() >= kMaxTuned) m->tuned.erase(m->tuned.begin());
+  m->tuned.push_back(e);
+}
+
+extern "C" int kin_resolve_options(kin_mech *m, int64_t n, double dt, const kin_options *opt,
+                                   kin_options *out) {
+  if (!m || !out || n < 0 || !(dt > 0.0) || !std::isfinite(dt)) return KIN_ERR_INVALID_ARG;
+  kin_options o;
+  if (opt) {
+    o = *opt;
+  } else {
+    kin_options_default(&o);
+  }
+  resolve_auto(m, n, dt, o);
+  *out = o;
+  return KIN_OK;
+}
+
 static int check_common(kin_mech *m, const void *Y, const void *T, const void *P, int64_t n,
                         double dt, double rtol, double atol) {
   if (!m || n < 0) return KIN_ERR_INVALID_ARG;
@@ -482,7 +560,8 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   } else {
     kin_options_default(&o);
   }
-  if (o.layout != KIN_LAYOUT_PLAIN && o.layout != KIN_LAYOUT_QUEUE && o.layout != KIN_LAYOUT_WARP)
+  if (o.layout != KIN_LAYOUT_PLAIN && o.layout != KIN_LAYOUT_QUEUE && o.layout != KIN_LAYOUT_WARP &&
+      o.layout != KIN_LAYOUT_AUTO)
     return KIN_ERR_INVALID_ARG;
   if (o.nit < 1 || o.nit > 50 || o.max_steps < 1) return KIN_ERR_INVALID_ARG;
   if (o.queue_refill < 0 || o.queue_refill > 32 || o.stop_after < 0) return KIN_ERR_INVALID_ARG;
@@ -491,6 +570,8 @@ extern "C" int kin_integrate_ex(kin_mech *m, double *Y, double *T, const double 
   if (o.lanes != 0 && o.lanes != 4 && o.lanes != 8 && o.lanes != 16 && o.lanes != 32)
     return KIN_ERR_INVALID_ARG;
   if (!(o.h_fixed >= 0.0) || !std::isfinite(o.h_fixed)) return KIN_ERR_INVALID_ARG;
+  if (o.block != 0 && (o.block < 32 || o.block > 64 || o.block % 32)) return KIN_ERR_INVALID_ARG;
+  resolve_auto(m, n, dt, o);
   if (o.h_fixed > 0.0 && o.layout == KIN_LAYOUT_WARP) return KIN_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   m->last_stream = st;
@@ -720,6 +801,7 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
     best->block = cands[0].block;
     best->queue_refill = cands[0].refill;
     best->lanes = cands[0].lanes;
+    remember_tuning(m, n, dt, *best);
     return KIN_OK;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -786,5 +868,6 @@ extern "C" int kin_autotune(kin_mech *m, const double *Y, const double *T, const
   best->block = cands[best_i].block;
   best->queue_refill = cands[best_i].refill;
   best->lanes = cands[best_i].lanes;
+  remember_tuning(m, n, dt, *best);
   return KIN_OK;
 }

@@ -1,4 +1,6 @@
 // kin_integrate_static: the one entry point of libkin that allocates nothing.
+// (The CUDA driver may still reserve local memory for a kernel's per-thread
+// frame at its first launch on a device; see include/kin.h.)
 //
 // Some callers cannot call cudaMalloc: code running inside a host framework
 // whose allocator owns (and has reserved) all device memory, plugins that are
@@ -15,6 +17,7 @@
 // (on different streams) race on it and must not be issued.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -59,6 +62,18 @@ extern "C" int kin_integrate_static(const kin_mech_desc *desc, double *Y, double
   if (!desc || n < 0 || (n > 0 && (!Y || !T || !P))) return KIN_ERR_INVALID_ARG;
   if (!(dt > 0.0) || !(rtol > 0.0) || !(atol > 0.0) || !std::isfinite(dt))
     return KIN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // The tables are uploaded from host vectors this call frees: a graph
+  // captured from it would replay copies from freed memory.  Refuse capture
+  // before any CUDA work is issued.
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return KIN_ERR_UNSUPPORTED;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return KIN_ERR_UNSUPPORTED;
+  }
   MechLayout L;
   std::vector<double> dtab;
   std::vector<int> itab;
@@ -72,7 +87,6 @@ extern "C" int kin_integrate_static(const kin_mech_desc *desc, double *Y, double
   unsigned char *base = nullptr;
   if ((rc = scratch_address(dev, &base))) return rc;
   KIN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  cudaStream_t st = (cudaStream_t)stream;
   double *tab = reinterpret_cast<double *>(base);
   int *itb = reinterpret_cast<int *>(base + dbytes);
   unsigned long long *totals = reinterpret_cast<unsigned long long *>(base + kTableBytes);
@@ -82,6 +96,10 @@ extern "C" int kin_integrate_static(const kin_mech_desc *desc, double *Y, double
   if (n == 0) return KIN_OK;
   kin_options o;
   kin_options_default(&o);
+  // the default options without a tuning cache or a per-mechanism
+  // workspace: one state per thread (the WARP layout needs Jacobian slots)
+  o.layout = KIN_LAYOUT_PLAIN;
+  o.block = 64;
   KernelArgs a;
   a.L = L;
   a.tab = tab;
@@ -109,7 +127,7 @@ extern "C" int kin_integrate_static(const kin_mech_desc *desc, double *Y, double
   a.rp.hfixed = 0.0;
   a.refill_min = 1;
   a.order = nullptr;
-  a.gscratch = nullptr;  // the default (QUEUE) layout needs no group slots
+  a.gscratch = nullptr;  // the thread layout needs no group slots
   a.gslots = 0;
   return launch_dispatch(a, o, st, sms);
 }

@@ -17,7 +17,9 @@ LIB_PATH = os.path.join(HERE, "libkin.so")
 
 KIN_OK, KIN_ERR_INVALID_ARG, KIN_ERR_CUDA, KIN_ERR_NOMEM, KIN_ERR_MECH = 0, 1, 2, 3, 4
 KIN_ERR_STATE_FAILED, KIN_ERR_UNSUPPORTED = 5, 6
-LAYOUT_PLAIN, LAYOUT_QUEUE, LAYOUT_WARP = 0, 1, 2
+LAYOUT_PLAIN, LAYOUT_QUEUE, LAYOUT_WARP, LAYOUT_AUTO = 0, 1, 2, 3
+LAYOUT_NAMES = {LAYOUT_PLAIN: "plain", LAYOUT_QUEUE: "queue", LAYOUT_WARP: "warp",
+                LAYOUT_AUTO: "auto"}
 KEY_GIVEN, KEY_STEP_HEURISTIC, KEY_GIVEN_LOG = 0, 1, 2
 COUNTER_NAMES = ("nstep", "naccpt", "nrejct", "nfcn", "njac", "ndec", "nsol", "status")
 MAX_SPECIES = 64
@@ -29,7 +31,8 @@ EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integra
            "kin_integrate_static", "kin_mlp_create", "kin_mlp_destroy", "kin_mlp_num_params",
            "kin_mlp_get_params", "kin_mlp_set_params", "kin_mlp_forward", "kin_mlp_grad",
            "kin_mlp_train_step", "kin_moments", "kin_mlp_features", "kin_mlp_targets",
-           "kin_mlp_predict", "kin_autotune", "kin_order_states", "kin_mlp_train_step_rows")
+           "kin_mlp_predict", "kin_autotune", "kin_order_states", "kin_mlp_train_step_rows",
+           "kin_resolve_options")
 
 
 class KinError(RuntimeError):
@@ -86,6 +89,7 @@ def lib():
             L.kin_integrate_static.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp]
             L.kin_autotune.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp, vp, i32, vp]
             L.kin_order_states.argtypes = [vp, vp, vp, vp, i64, d, d, i32, vp, vp, vp]
+            L.kin_resolve_options.argtypes = [vp, i64, d, vp, vp]
             L.kin_mlp_create.argtypes = [i32, i32, i32, i32, C.c_uint64, C.POINTER(vp)]
             L.kin_mlp_destroy.argtypes = [vp]
             L.kin_mlp_destroy.restype = None
@@ -129,13 +133,12 @@ def _stream(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
-def options(layout="queue", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7, block=0,
+def options(layout="auto", lu_fp32=False, jac_fd=False, max_steps=100000, nit=7, block=0,
             grid_per_sm=0, transform_tol=True, queue_refill=0, stop_after=0, h0=None, z0=None,
             h_first=None, z_first=None, order=None, lanes=0, h_fixed=0.0, order_by=None):
     o = Options()
     _check(lib().kin_options_default(C.byref(o)), "kin_options_default")
-    o.layout = {"plain": LAYOUT_PLAIN, "queue": LAYOUT_QUEUE, "warp": LAYOUT_WARP}[layout] \
-        if isinstance(layout, str) \
+    o.layout = {v: k for k, v in LAYOUT_NAMES.items()}[layout] if isinstance(layout, str) \
         else int(layout)
     o.lu_fp32 = int(bool(lu_fp32))
     o.jac_fd = int(bool(jac_fd))
@@ -287,9 +290,19 @@ class Mechanism:
                                 secs.ctypes.data, 16, _stream(stream))
         _check(rc, "kin_autotune")
         secs = secs[~np.isnan(secs)]
-        layout = {LAYOUT_PLAIN: "plain", LAYOUT_QUEUE: "queue", LAYOUT_WARP: "warp"}[best.layout]
-        return dict(layout=layout, block=best.block, queue_refill=best.queue_refill,
-                    grid_per_sm=best.grid_per_sm, lanes=best.lanes), secs.tolist()
+        return dict(layout=LAYOUT_NAMES[best.layout], block=best.block,
+                    queue_refill=best.queue_refill, grid_per_sm=best.grid_per_sm,
+                    lanes=best.lanes), secs.tolist()
+
+    def resolve(self, n, dt, **opt):
+        """kin_resolve_options: the launch configuration an integration of n
+        states over dt with these options would use (layout "auto" resolved)."""
+        o = options(**opt)
+        out = Options()
+        _check(lib().kin_resolve_options(self.handle, int(n), float(dt), C.byref(o),
+                                         C.byref(out)), "kin_resolve_options")
+        return dict(layout=LAYOUT_NAMES[out.layout], block=out.block,
+                    queue_refill=out.queue_refill, lanes=out.lanes)
 
     def order_states(self, Y, T, P, rtol=1e-6, atol=1e-10, *, key=None, given_key=None,
                      log_key=False, order=None, stream=None):

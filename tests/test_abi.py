@@ -40,7 +40,7 @@ def test_radau_constants_match_oracle_derivation():
 
 def test_options_defaults():
     o = kin.options()
-    assert (o.layout, o.lu_fp32, o.jac_fd, o.max_steps, o.nit, o.transform_tol) == (1, 0, 0,
+    assert (o.layout, o.lu_fp32, o.jac_fd, o.max_steps, o.nit, o.transform_tol) == (3, 0, 0,
                                                                                      100000, 7, 1)
     assert kin.lib().kin_options_default(None) == kin.KIN_ERR_INVALID_ARG
 

@@ -1,7 +1,9 @@
 """The step/guess predictor's CUDA kernels against the FP64 numpy reference
-(oracle/mlp.py): forward values, loss gradients (BF16 tensor-core mode to
-~2 %, FP32 check mode to 1e-5), Adam training progress, and the feature /
-target / prediction kernels that connect it to the integrator."""
+(oracle/mlp.py), entry by entry: forward values and loss gradients (FP32
+check mode to 1e-5 of each block's scale; BF16 tensor-core mode within the
+propagated BF16 rounding bound), an Adam step, the prediction entry point,
+training progress, and the feature / target kernels that connect the
+network to the integrator."""
 import numpy as np
 import pytest
 
@@ -36,9 +38,61 @@ def bf16(x):
     return torch.from_numpy(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 3e-2)])
+U_BF16 = 2.0 ** -8      # a BF16 rounding flip moves a value by at most 2^-8 of it
+U_ACC = 2.0 ** -20      # FP32 accumulation and __expf, relative to the absolute terms
+
+
+def bf16_bounds(W, b, cache, y, t):
+    """First-order element-wise bounds on |GPU - reference| for the BF16 mode.
+
+    Both sides round the same FP32 values at the same points (input, hidden
+    activations, back-propagated gradient); they differ by FP32 accumulation
+    and, where a value lies near a rounding boundary, by one BF16 step of
+    that value.  Those differences are propagated layer by layer through
+    absolute-value products, with |silu'| <= 1.1 and |silu''| <= 0.5."""
+    h, a = cache
+    L = len(W)
+    aW = [np.abs(w) for w in W]
+    Eh = np.zeros_like(h[0])                                   # the input is rounded alike
+    EC = []
+    for l in range(L):
+        E = Eh @ aW[l] + U_ACC * (np.abs(h[l]) @ aW[l])
+        EC.append(E)
+        if l < L - 1:
+            Eh = 1.1 * E + U_BF16 * np.abs(h[l + 1])
+    Ey = EC[-1]
+    g = 2.0 * (y - t) / y.size
+    Eg = 2.0 * Ey / y.size
+    EW, Eb = [None] * L, [None] * L
+    hin_err = [np.zeros_like(h[0])] + [1.1 * EC[l] + U_BF16 * np.abs(h[l + 1])
+                                       for l in range(L - 1)]
+    for l in range(L - 1, -1, -1):
+        if l < L - 1:
+            sg = 1.1 * np.ones_like(a[l])
+            Eg = Eg * sg + np.abs(g) * 0.5 * EC[l]
+            g = g * M.silu_grad(a[l])
+        Egr = Eg + U_BF16 * np.abs(g)
+        EW[l] = (hin_err[l].T @ np.abs(g) + np.abs(h[l]).T @ Egr
+                 + U_ACC * (np.abs(h[l]).T @ np.abs(g)))
+        Eb[l] = Eg.sum(axis=0) + U_ACC * np.abs(g).sum(axis=0)
+        dH = g @ W[l].T
+        Eg = Egr @ aW[l].T + U_ACC * (np.abs(g) @ aW[l].T)
+        g = dH
+    return Ey, EW, Eb
+
+
+def flat(Ws, bs):
+    return np.concatenate([np.concatenate([a.ravel(), c]) for a, c in zip(Ws, bs)])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 @pytest.mark.parametrize("din,w,dout,n", [(16, 64, 40, 77), (56, 32, 160, 130)])
-def test_forward_and_gradients_against_fp64_reference(precision, tol, din, w, dout, n):
+def test_forward_and_gradients_against_fp64_reference(precision, din, w, dout, n):
+    """Every output and every gradient entry against the FP64 reference.
+    FP32 mode: |gpu - ref| <= 1e-5 (|ref| + the block's largest |ref|), block
+    by block (each W_l, each b_l, the output).  BF16 mode: the reference
+    rounds to BF16 where the kernels do, and each entry must lie within the
+    propagated rounding bound of bf16_bounds."""
     rng = np.random.default_rng(din + w)
     net = kin.MLP(din, w, dout, precision=precision, seed=3)
     p = net.get_params()
@@ -54,17 +108,68 @@ def test_forward_and_gradients_against_fp64_reference(precision, tol, din, w, do
     net.grad(Xd, Td, grad_out=g, loss_out=loss)
     W, b = unpack(p.astype(np.float64), din, w, dout)
     x = X.astype(np.float64)
-    if precision == "bf16":
+    t = T.astype(np.float64)
+    rnd = bf16 if precision == "bf16" else None
+    if rnd is not None:
         W = [bf16(Wl) for Wl in W]
-        x = bf16(x)
-    y, cache = M.forward(W, b, x)
-    gW, gb = M.backward(W, b, cache, y, T.astype(np.float64))
-    ref = np.concatenate([np.concatenate([a.ravel(), c]) for a, c in zip(gW, gb)])
-    yg = Y.cpu().numpy()
-    assert np.linalg.norm(yg - y) / np.linalg.norm(y) < tol
+    y, cache = M.forward(W, b, x, rnd=rnd)
+    gW, gb = M.backward(W, b, cache, y, t, rnd=rnd)
+    yg = Y.cpu().numpy().astype(np.float64)
     gg = g.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(gg - ref) / np.linalg.norm(ref) < tol
-    assert abs(loss.item() - M.loss(y, T)) / M.loss(y, T) < tol
+    gWg, gbg = unpack(gg, din, w, dout)
+    if precision == "fp32":
+        def bound(ref):
+            return 1e-5 * (np.abs(ref) + np.abs(ref).max())
+        blocks = [("y", yg, y, bound(y))]
+        blocks += [(f"W{l}", gWg[l], gW[l], bound(gW[l])) for l in range(4)]
+        blocks += [(f"b{l}", gbg[l], gb[l], bound(gb[l])) for l in range(4)]
+    else:
+        Ey, EW, Eb = bf16_bounds(W, b, cache, y, t)
+        blocks = [("y", yg, y, Ey + 1e-6 * np.abs(y))]
+        blocks += [(f"W{l}", gWg[l], gW[l], EW[l] + 1e-6 * np.abs(gW[l])) for l in range(4)]
+        blocks += [(f"b{l}", gbg[l], gb[l], Eb[l] + 1e-6 * np.abs(gb[l])) for l in range(4)]
+    worst = {}
+    for name, got, ref, bnd in blocks:
+        assert got.shape == ref.shape, name
+        ratio = np.abs(got - ref) / (bnd + 1e-30)
+        worst[name] = float(ratio.max())
+        assert np.all(np.abs(got - ref) <= bnd), (name, np.unravel_index(ratio.argmax(), ratio.shape),
+                                                   worst[name])
+    print(f"\n{precision} {din}x{w}x{dout} n={n}: largest |gpu - ref| / bound per block "
+          + ", ".join(f"{k} {v:.2f}" for k, v in worst.items()))
+    L0 = M.loss(y, t)
+    assert abs(loss.item() - L0) <= (1e-5 if precision == "fp32" else 2e-2) * L0
+
+
+def test_adam_step_against_the_reference():
+    """One FP32-mode Adam step from zero moments: every parameter moves as the
+    reference's Adam (bias-corrected, beta 0.9 / 0.999, eps 1e-8) moves it
+    with the reference gradient."""
+    rng = np.random.default_rng(8)
+    din, w, dout, n = 12, 32, 10, 50
+    net = kin.MLP(din, w, dout, precision="fp32", seed=4)
+    p = net.get_params()
+    p[:] += rng.normal(0, 0.01, p.size).astype(np.float32)
+    net.set_params(p)
+    X = rng.normal(size=(n, din)).astype(np.float32)
+    T = rng.normal(size=(n, dout)).astype(np.float32)
+    lr = 1e-3
+    net.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), lr)
+    torch.cuda.synchronize()
+    p1 = net.get_params().astype(np.float64)
+    W, b = unpack(p.astype(np.float64), din, w, dout)
+    y, cache = M.forward(W, b, X.astype(np.float64))
+    gW, gb = M.backward(W, b, cache, y, T.astype(np.float64))
+    params = [q for pair in zip(W, b) for q in pair]
+    grads = [q for pair in zip(gW, gb) for q in pair]
+    opt = M.Adam(params, lr=lr)
+    opt.step(params, grads)
+    ref = flat(params[0::2], params[1::2])
+    # the first step moves each parameter by lr g/(|g| + eps): about lr, sign of g
+    gflat = flat(grads[0::2], grads[1::2])
+    sig = np.abs(gflat) > 1e-4          # away from the eps-dominated tiny gradients
+    np.testing.assert_allclose(p1[sig], ref[sig], rtol=0, atol=2e-3 * lr + 1e-6)
+    assert np.all(np.abs(p1[~sig] - p.astype(np.float64)[~sig]) <= 1.01 * lr + 1e-6)
 
 
 def test_training_reduces_loss_on_device():
@@ -118,6 +223,56 @@ def test_feature_target_and_prediction_kernels():
     h0n = h0.cpu().numpy()
     assert np.all(np.isfinite(h0n)) and np.all(h0n <= 1e-4) and np.all(h0n >= 1e-14)
     assert np.all(np.isfinite(z0.cpu().numpy()))
+
+
+def test_prediction_matches_the_reference_network():
+    """kin_mlp_predict on a network with set weights (FP32 mode) against the
+    FP64 reference: features, forward pass, de-standardisation, exp and the
+    clip of h0 to [1e-14, dt], and the stage guesses z0 [3 ns][n], entry by
+    entry."""
+    mech = synth.make_mechanism("h2")
+    st = synth.make_states(mech, 200, seed=9)
+    ns, n, dt = mech.ns, st.n, 1e-4
+    din, dout, w = 3 + ns, 1 + 3 * ns, 48
+    rng = np.random.default_rng(12)
+    net = kin.MLP(din, w, dout, precision="fp32", seed=6)
+    p = net.get_params()
+    p[:] = (0.5 * p + rng.normal(0, 0.05, p.size)).astype(np.float32)
+    net.set_params(p)
+    Y, T, P = (torch.from_numpy(a).cuda() for a in (st.Y, st.T, st.P))
+    X = torch.empty((n, din), dtype=torch.float32, device="cuda")
+    kin.features(ns, Y, T, P, dt, X)
+    xm = X.cpu().numpy().astype(np.float64)
+    in_mean = xm.mean(0).astype(np.float32)
+    in_std = np.maximum(xm.std(0), 1e-3).astype(np.float32)
+    out_mean = np.concatenate([[np.log(3e-7)], rng.normal(0, 1e-9, 3 * ns)]).astype(np.float32)
+    out_std = np.concatenate([[4.0], np.full(3 * ns, 1e-8)]).astype(np.float32)
+    norm = {k: torch.from_numpy(v).cuda() for k, v in
+            dict(in_mean=in_mean, in_std=in_std, out_mean=out_mean, out_std=out_std).items()}
+    h0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    z0 = torch.empty((3 * ns, n), dtype=torch.float64, device="cuda")
+    net.predict(ns, Y, T, P, dt, norm, h0=h0, z0=z0)
+    torch.cuda.synchronize()
+    # reference: FP32 standardised features (as the kernel stores them), FP64 network
+    xs = ((X.cpu().numpy() - in_mean) / in_std).astype(np.float64)
+    W, b = unpack(p.astype(np.float64), din, w, dout)
+    y, _ = M.forward(W, b, xs)
+    lh = y[:, 0] * out_std[0] + out_mean[0]
+    h_ref = np.clip(np.exp(lh), 1e-14, dt)
+    z_ref = (y[:, 1:] * out_std[1:] + out_mean[1:]).T
+    scale = np.abs(y).max(axis=0)
+    # |dy| <= 1e-5 of the output's scale: h0 relative error |dlh| = std |dy|
+    np.testing.assert_allclose(h0.cpu().numpy(), h_ref, rtol=1e-5 * out_std[0] * scale[0] + 1e-6)
+    assert np.mean((h_ref > 1e-14) & (h_ref < dt)) > 0.5       # mostly inside the clip
+    zb = 1e-5 * (scale[1:] * out_std[1:])[:, None] + 1e-6 * np.abs(z_ref)
+    assert np.all(np.abs(z0.cpu().numpy() - z_ref) <= zb)
+    # the clip: outputs pushed far out of range land on the bounds
+    big = dict(norm, out_mean=norm["out_mean"] + 100.0)
+    net.predict(ns, Y, T, P, dt, big, h0=h0)
+    assert np.all(h0.cpu().numpy() == dt)
+    small = dict(norm, out_mean=norm["out_mean"] - 200.0)
+    net.predict(ns, Y, T, P, dt, small, h0=h0)
+    assert np.all(h0.cpu().numpy() == 1e-14)
 
 
 def test_trained_predictor_removes_steps_at_equal_error():

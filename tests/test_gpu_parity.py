@@ -202,9 +202,8 @@ def test_h2_dt_1e4_mixed_parity(h2):
     eT, eY, per = parity(Yg, Tg, Yo, To)
     # stiff ignition states amplify rounding differences once a decision flips;
     # all but a handful must meet the bar and all must stay close
-    frac = np.mean(per <= RTOL_PARITY)
-    assert frac >= 0.99, (frac, eT, eY)
-    assert eT <= 1e-3
+    # FP64 matrices follow the oracle's decisions: every state meets the bar
+    assert eT <= RTOL_PARITY and eY <= RTOL_PARITY, (eT, eY, np.argsort(per)[-5:])
 
 
 def test_ch4_parity(ch4):
@@ -214,7 +213,7 @@ def test_ch4_parity(ch4):
     Yg, Tg, cg, sg = run_gpu(mg, st, 1e-6, layout="queue")
     assert np.all(sg == 0)
     eT, eY, per = parity(Yg, Tg, Yo, To)
-    assert np.mean(per <= RTOL_PARITY) >= 0.97, (eT, eY)
+    assert eT <= RTOL_PARITY and eY <= RTOL_PARITY, (eT, eY, np.argsort(per)[-5:])
 
 
 def test_fd_jacobian_integration_parity(ch4):
@@ -486,13 +485,42 @@ def test_host_entry_matches_device_entry(h2):
                       order_by="heuristic")
 
 
-def test_default_entry_is_queue_fp64(h2):
-    mech, mg, st = h2
-    st = st.subset(np.arange(100))
+def test_default_entry_uses_the_size_rule_then_the_tuning(h2, ch4):
+    """kin_integrate (default options: layout AUTO) runs PLAIN with FP64
+    matrices on a 13-species mechanism before any tuning, the autotuner's
+    choice after it, and WARP on a 53-species mechanism: never the
+    per-thread 64-species kernel."""
+    mech, _, st = h2
+    mg = kin.Mechanism(mech)                      # a fresh tuning cache
+    st = st.subset(np.arange(300))
+    assert mg.resolve(st.n, 1e-6) == dict(layout="plain", block=64, queue_refill=0, lanes=0)
     Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
     mg.integrate_default(Y, T, P, 1e-6)
-    Yq, Tq, _, _ = run_gpu(mg, st, 1e-6, layout="queue")
-    np.testing.assert_array_equal(T.cpu().numpy(), Tq)
+    Yp, Tp, _, _ = run_gpu(mg, st, 1e-6, layout="plain")
+    np.testing.assert_array_equal(T.cpu().numpy(), Tp)
+    np.testing.assert_array_equal(Y.cpu().numpy(), Yp)
+    best, _ = mg.autotune(Y, T, P, 1e-6)
+    got = mg.resolve(st.n, 1e-6)
+    assert got == {k: best[k] for k in ("layout", "block", "queue_refill", "lanes")}
+    # another decade of dt or another precision has no tuning yet: the size rule
+    assert mg.resolve(st.n, 1e-4)["layout"] == "plain"
+    assert mg.resolve(st.n, 1e-6, lu_fp32=True)["layout"] == "plain"
+    Y, T = dev(st.Y), dev(st.T)
+    mg.integrate_default(Y, T, P, 1e-6)
+    Yb, Tb, _, _ = run_gpu(mg, st, 1e-6, **{k: v for k, v in got.items()})
+    np.testing.assert_array_equal(T.cpu().numpy(), Tb)
+    np.testing.assert_array_equal(Y.cpu().numpy(), Yb)
+    # 53 species: WARP with 32 lanes, before and after tuning, also in FP32
+    mech4, mg4, st4 = ch4
+    for f32 in (False, True):
+        assert mg4.resolve(64, 1e-6, lu_fp32=f32)["layout"] == "warp"
+    sub = st4.subset(np.arange(40))
+    Y, T, P = dev(sub.Y), dev(sub.T), dev(sub.P)
+    mg4.integrate_default(Y, T, P, 1e-6)
+    Yw, Tw, _, _ = run_gpu(mg4, sub, 1e-6, layout="warp", lanes=32)
+    np.testing.assert_array_equal(T.cpu().numpy(), Tw)
+    # a fixed step cannot run in WARP: AUTO falls back to PLAIN
+    assert mg4.resolve(64, 1e-6, h_fixed=1e-8)["layout"] == "plain"
 
 
 # ----------------------------------------------------------------------------
@@ -512,12 +540,126 @@ def test_full_size_mixed_sampled_parity(dt):
     sub = st.subset(idx)
     Yo, To, co = O.integrate(mech, sub, dt)
     eT, eY, per = parity(Yg[:, idx], Tg[idx], Yo, To)
-    assert np.mean(per <= RTOL_PARITY) >= 0.97, (eT, eY)
+    assert eT <= RTOL_PARITY and eY <= RTOL_PARITY, (eT, eY, np.argsort(per)[-5:])
     # properties that hold at any size
     np.testing.assert_allclose(Yg.sum(axis=0), 1.0, atol=1e-12)
     el0 = (mech.comp.T.astype(float) / mech.W[None, :]) @ st.Y
     el1 = (mech.comp.T.astype(float) / mech.W[None, :]) @ Yg
     np.testing.assert_allclose(el1, el0, rtol=1e-9, atol=1e-13)
+
+
+# A state ignites over the step when the oracle's temperature changes by more
+# than this.  There the result is sensitive to the internal step sequence, and
+# FP32 Newton matrices may take another (equally valid) sequence: such states
+# are held to the tolerance-level bound E_i <= 1 and reported, every other
+# state to the strict bar (the non-igniting fraction).
+IGNITION_DT_K = 10.0
+
+
+def split_report(tag, Yg, Tg, Yo, To, T0):
+    """Per-state bar, the non-igniting mask and E_i (Sec. 2.3) against the oracle."""
+    eT, eY, per = parity(Yg, Tg, Yo, To)
+    relT = np.abs(Tg - To) / np.abs(To)
+    quiet = np.abs(To - T0) <= IGNITION_DT_K
+    E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), np.concatenate([To[None], Yo[:-1]]))
+    ig = ~quiet
+    print(f"\n{tag}: {per.size} states, {quiet.sum()} non-igniting (max per-state error "
+          f"{per[quiet].max() if quiet.any() else 0:.3g}), {ig.sum()} igniting; all states: "
+          f"{np.mean(per <= RTOL_PARITY):.4f} within 1e-5, max rel T {relT.max():.3g}, "
+          f"E max {E.max():.3g} / p99 {np.percentile(E, 99):.3g} / median {np.median(E):.3g}"
+          + (f"; igniting: E max {E[ig].max():.3g}, {np.mean(per[ig] <= RTOL_PARITY):.3f} "
+             f"within 1e-5" if ig.any() else ""))
+    return per, relT, quiet, E
+
+
+@pytest.mark.parametrize("dt", [1e-4, 1e-6])
+def test_benchmarked_path_parity(dt):
+    """Exactly what bench.py times: the 2^20 mixed H2 states, PLAIN with 64
+    threads, FP32 Newton matrices, states ordered by the starting-step
+    heuristic, one CUDA-graph replay.  512 sampled states (and the first and
+    last) against the FP64 oracle: every non-igniting state meets 1e-5 in T
+    and in every species above 1e-8, T meets it on every state, and every
+    state is within the tolerance (E_i <= 1)."""
+    mech, st, _ = synth.workload("h2_mixed_2p20")
+    mg = kin.Mechanism(mech)
+    Y, T, P = dev(st.Y), dev(st.T), dev(st.P)
+    Y0, T0 = Y.clone(), T.clone()
+    status = torch.full((st.n,), -1, dtype=torch.int32, device="cuda")
+    g = mg.capture(Y, T, P, dt, status=status, layout="plain", block=64, lu_fp32=True,
+                   order_by="heuristic")
+    Y.copy_(Y0)
+    T.copy_(T0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert int((status != 0).sum()) == 0
+    rng = np.random.default_rng(20261204)
+    idx = np.unique(np.concatenate([rng.choice(st.n, size=512, replace=False), [0, st.n - 1]]))
+    sub = st.subset(idx)
+    Yo, To, co = O.integrate(mech, sub, dt)
+    assert np.all(co[:, 7] == 0)
+    Yg, Tg = Y.cpu().numpy()[:, idx], T.cpu().numpy()[idx]
+    per, relT, quiet, E = split_report(f"benchmarked path, dt={dt:g}", Yg, Tg, Yo, To, sub.T)
+    assert quiet.sum() >= 32
+    assert np.all(per[quiet] <= RTOL_PARITY), (idx[quiet][per[quiet] > RTOL_PARITY])
+    assert relT.max() <= RTOL_PARITY
+    assert E.max() <= 1.0, E.max()
+    assert np.mean(per <= RTOL_PARITY) >= 0.99
+    np.testing.assert_allclose(Y.cpu().numpy().sum(axis=0), 1.0, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def ch4_config3_sample():
+    mech, st, _ = synth.workload("ch4_2p18")
+    rng = np.random.default_rng(4404)
+    idx = np.sort(rng.choice(st.n, size=160, replace=False))
+    sub = st.subset(idx)
+    return mech, kin.Mechanism(mech), sub, O.integrate(mech, sub, 1e-4)
+
+
+def test_ch4_config3_fp64_warp_parity(ch4_config3_sample):
+    """Configuration 3's states (53 species, 325 reactions, dt = 1e-4 s) in the
+    WARP layout with FP64 matrices: every sampled state meets the strict bar."""
+    mech, mg, sub, (Yo, To, co) = ch4_config3_sample
+    Yg, Tg, cg, sg = run_gpu(mg, sub, 1e-4, layout="warp")
+    assert np.all(sg == 0) and np.all(co[:, 7] == 0)
+    per, relT, quiet, E = split_report("CH4 config 3, WARP FP64", Yg, Tg, Yo, To, sub.T)
+    assert np.all(per <= RTOL_PARITY), np.sort(per)[-5:]
+    assert np.mean(np.all(cg[:, :7] == co[:, :7], axis=1)) >= 0.95
+
+
+def test_ch4_config3_fp32_warp_error(ch4_config3_sample):
+    """Configuration 3 as specified: WARP layout, FP32 Newton matrices, dt =
+    1e-4 s, against the FP64 oracle.  FP32 iteration matrices change the
+    simplified-Newton iterates and iteration counts, and the step-size
+    controller's safety factor depends on the count, so some states take
+    another internal step sequence: a different integration at the same
+    tolerance.  T meets the strict bar on every state and at least 90 % of
+    the states meet it in every species.  Equal accuracy: against a
+    tight-tolerance reference (the oracle at rtol 1e-10, atol 1e-17,
+    untransformed) on 24 seeded states plus every state that misses the
+    strict bar, the FP32 results' E_i (Sec. 2.3) stay within twice the FP64
+    oracle's own, in the maximum and in the median."""
+    mech, mg, sub, (Yo, To, co) = ch4_config3_sample
+    Yg, Tg, cg, sg = run_gpu(mg, sub, 1e-4, layout="warp", lu_fp32=True)
+    assert np.all(sg == 0)
+    per, relT, quiet, E = split_report("CH4 config 3, WARP FP32", Yg, Tg, Yo, To, sub.T)
+    print(f"same step/Newton/J/LU counts as the oracle: "
+          f"{np.mean(np.all(cg[:, :7] == co[:, :7], axis=1)):.3f}")
+    assert relT.max() <= RTOL_PARITY, relT.max()
+    assert np.mean(per <= RTOL_PARITY) >= 0.90
+    rng = np.random.default_rng(909)
+    sel = np.union1d(rng.choice(sub.n, size=24, replace=False), np.where(per > RTOL_PARITY)[0])
+    Yx, Tx, cx = O.integrate(mech, sub.subset(sel), 1e-4, rtol=1e-10, atol=1e-17,
+                             transform_tol=False)
+    assert np.all(cx[:, 7] == 0)
+    yx = np.concatenate([Tx[None], Yx[:-1]])
+    E32 = O.error_norm(np.concatenate([Tg[None], Yg[:-1]])[:, sel], yx)
+    E64 = O.error_norm(np.concatenate([To[None], Yo[:-1]])[:, sel], yx)
+    print(f"E against the tight reference on {sel.size} states: FP32 max {E32.max():.3g} "
+          f"median {np.median(E32):.3g}; FP64 oracle max {E64.max():.3g} median "
+          f"{np.median(E64):.3g}")
+    assert E32.max() <= 2.0 * E64.max(), (E32.max(), E64.max())
+    assert np.median(E32) <= 2.0 * np.median(E64), (np.median(E32), np.median(E64))
 
 
 # ----------------------------------------------------------------------------
@@ -600,7 +742,7 @@ def test_warp_layout_h2_parity(h2, h2_oracle, lu_fp32, lanes):
     assert np.all(sg == 0)
     eT, eY, per = parity(Yg, Tg, Yo, To)
     if not lu_fp32:
-        assert np.mean(per <= RTOL_PARITY) >= 0.99, (eT, eY)
+        assert eT <= RTOL_PARITY and eY <= RTOL_PARITY, (eT, eY, np.argsort(per)[-5:])
         same = np.all(cg[:, :7] == co[:, :7], axis=1)
         assert same.mean() >= 0.95, same.mean()
     E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), np.concatenate([To[None], Yo[:-1]]))
@@ -614,7 +756,7 @@ def test_warp_layout_ch4_parity(ch4):
     Yg, Tg, cg, sg = run_gpu(mg, st, 1e-6, layout="warp")
     assert np.all(sg == 0)
     eT, eY, per = parity(Yg, Tg, Yo, To)
-    assert np.mean(per <= RTOL_PARITY) >= 0.95, (eT, eY)
+    assert eT <= RTOL_PARITY and eY <= RTOL_PARITY, (eT, eY, np.argsort(per)[-5:])
     Yf, Tf, cf, sf = run_gpu(mg, st, 1e-6, layout="warp", lu_fp32=True)
     assert np.all(sf == 0)
     E = O.error_norm(np.concatenate([Tf[None], Yf[:-1]]), np.concatenate([To[None], Yo[:-1]]))

@@ -74,3 +74,28 @@ def test_training_reduces_loss():
         gW, gb = M.backward(W, b, c, y, t)
         opt.step(W + b, gW + gb)
     assert M.loss(M.forward(W, b, x)[0], t) < 0.2 * l0
+
+
+def test_rounding_points_of_the_reduced_precision_mode():
+    """With rnd, the input and every hidden activation are rounded before the
+    next product and the output is not; the back-propagated gradient is
+    rounded where the products read it and the bias gradient sums it
+    unrounded.  A chain of one-unit layers makes each point visible."""
+    q = lambda v: np.round(np.asarray(v) * 8.0) / 8.0        # a coarse rounding, step 1/8
+    W = [np.array([[1.0]]), np.array([[1.0]]), np.array([[1.0]]), np.array([[3.0]])]
+    b = [np.array([0.0]), np.array([0.0]), np.array([0.0]), np.array([0.01])]
+    x = np.array([[1.3]])                                   # q(1.3) = 1.25
+    y, (h, a) = M.forward(W, b, x, rnd=q)
+    v = 1.25
+    for _ in range(3):
+        v = q(M.silu(v))
+    assert abs(y[0, 0] - (3.0 * v + 0.01)) < 1e-15          # output unrounded
+    assert h[0][0, 0] == 1.25 and all(hh[0, 0] == q(hh[0, 0]) for hh in h[1:4])
+    t = np.array([[0.0]])
+    gW, gb = M.backward(W, b, (h, a), y, t, rnd=q)
+    g = 2.0 * y[0, 0]
+    assert abs(gb[3][0] - g) < 1e-15                        # bias: unrounded
+    assert abs(gW[3][0, 0] - h[3][0, 0] * q(g)) < 1e-15     # weight: rounded g
+    yn, cn = M.forward(W, b, x)
+    gWn, gbn = M.backward(W, b, cn, yn, t)
+    assert abs(gbn[3][0] - 2.0 * yn[0, 0]) < 1e-15 and yn[0, 0] != y[0, 0]
