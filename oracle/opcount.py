@@ -176,10 +176,16 @@ def sqrt(x):
 # ---------------------------------------------------------------------------
 
 def mech_digest(mech) -> str:
-    """Digest of a mechanism's arrays (identifies the mechanism a count is for)."""
+    """Digest of a mechanism's structure: species and reaction counts, the
+    reactant/product slots, the reaction types and which efficiencies differ
+    from 1.  The counts depend on nothing else, and the digest does not
+    change with the last bits of the coefficients (which can differ between
+    hosts that generate the same seeded mechanism)."""
     h = hashlib.sha256()
-    for name in ("W", "nasa", "reac", "prod", "arrh", "rtype", "eff", "fall"):
-        h.update(np.ascontiguousarray(getattr(mech, name)).tobytes())
+    h.update(np.array([int(mech.ns), int(mech.nr)], dtype=np.int64).tobytes())
+    for name in ("reac", "prod", "rtype"):
+        h.update(np.ascontiguousarray(getattr(mech, name), dtype=np.int64).tobytes())
+    h.update(np.ascontiguousarray(np.asarray(mech.eff) != 1.0).tobytes())
     return h.hexdigest()[:16]
 
 

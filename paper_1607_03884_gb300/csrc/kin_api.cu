@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
@@ -288,6 +289,9 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
   L.ns = ns;
   L.nr = nr;
   L.neff = neff;
+  L.ntroe = ntroe;
+  L.nfall = 0;
+  for (int i = 0; i < nr; ++i) L.nfall += d->rtype[i] != 0;
   int o = 0;
   L.dW = o; o += ns;
   L.dinvW = o; o += ns;
@@ -308,14 +312,34 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
   L.ieff0 = q; q += nr;
   L.itroe = q;
   L.ieffsp = q; q += (neff > 0 ? neff : 1);
+  // Device order of the reactions: Troe falloff first, then third-body, then
+  // elementary, each by reactant and product count (stable).  Kernels that
+  // spread reactions over lanes then meet the falloff branches in the first
+  // rounds only and run the slot loops with equal trip counts; results
+  // depend on the order only through summation rounding.
+  std::vector<int> perm(nr);
+  for (int i = 0; i < nr; ++i) perm[i] = i;
+  auto rkey = [&](int i) {
+    int nre = 0, npr = 0;
+    for (int s2 = 0; s2 < 3; ++s2) {
+      nre += d->reac[3 * i + s2] >= 0;
+      npr += d->prod[3 * i + s2] >= 0;
+    }
+    const int t = d->rtype[i], cls = t == 2 ? 0 : t == 1 ? 1 : 2;
+    return cls * 16 + nre * 4 + npr;
+  };
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return rkey(a) < rkey(b); });
   // species-major list of (reaction, net coefficient) for gathered production rates
   std::vector<std::vector<int>> sp_list(ns);
-  for (int i = 0; i < nr; ++i)
+  for (int i = 0; i < nr; ++i) {
+    const int src = perm[i];
     for (int k = 0; k < ns; ++k) {
       int nu = 0;
-      for (int s2 = 0; s2 < 3; ++s2) nu += (d->prod[3 * i + s2] == k) - (d->reac[3 * i + s2] == k);
+      for (int s2 = 0; s2 < 3; ++s2)
+        nu += (d->prod[3 * src + s2] == k) - (d->reac[3 * src + s2] == k);
       if (nu != 0) sp_list[k].push_back((i << 4) | (nu + 8));
     }
+  }
   int ncsr = 0;
   for (int k = 0; k < ns; ++k) ncsr += (int)sp_list[k].size();
   L.icsr0 = q; q += ns + 1;
@@ -347,20 +371,21 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
   for (int j = 0; j < EXP_TAB; ++j) dt[L.dexp + j] = (double)exp2l((long double)j / EXP_TAB);
   int e = 0, tr = 0;
   for (int i = 0; i < nr; ++i) {
-    dt[L.dlnA + i] = std::log(d->arrh[3 * i]);
-    dt[L.db + i] = d->arrh[3 * i + 1];
-    dt[L.dTh + i] = d->arrh[3 * i + 2];
+    const int src = perm[i];  // description index of device reaction i
+    dt[L.dlnA + i] = std::log(d->arrh[3 * src]);
+    dt[L.db + i] = d->arrh[3 * src + 1];
+    dt[L.dTh + i] = d->arrh[3 * src + 2];
     int nre = 0, npr = 0;
     for (int s = 0; s < 3; ++s) {
-      if (d->reac[3 * i + s] >= 0) it[L.islot + 6 * i + nre++] = d->reac[3 * i + s];
-      if (d->prod[3 * i + s] >= 0) it[L.islot + 6 * i + 3 + npr++] = d->prod[3 * i + s];
+      if (d->reac[3 * src + s] >= 0) it[L.islot + 6 * i + nre++] = d->reac[3 * src + s];
+      if (d->prod[3 * src + s] >= 0) it[L.islot + 6 * i + 3 + npr++] = d->prod[3 * src + s];
     }
-    const int t = d->rtype[i];
+    const int t = d->rtype[src];
     int ne = 0;
     it[L.ieff0 + i] = e;
     if (t != 0) {
       for (int k = 0; k < ns; ++k) {
-        const double ef = d->eff[(size_t)i * ns + k];
+        const double ef = d->eff[(size_t)src * ns + k];
         if (ef != 1.0) {
           dt[L.deff + e] = ef - 1.0;
           it[L.ieffsp + e] = k;
@@ -372,7 +397,7 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
     if (ne > 255) return KIN_ERR_MECH;
     int troe_idx = 0;
     if (t == 2) {
-      const double *f = d->fall + 7 * i;
+      const double *f = d->fall + 7 * src;
       double *tp = &dt[L.dtroe + NTROE * tr];
       tp[0] = std::log(f[0]);
       tp[1] = f[1];

@@ -27,6 +27,7 @@ constexpr double LN10 = 2.302585092994045684;
 // ---------------------------------------------------------------------------
 struct MechLayout {
   int ns, nr, neff;
+  int ntroe, nfall;  // device order: Troe reactions [0, ntroe), third-body [ntroe, nfall)
   int nd, ni;  // table sizes in doubles / ints
   // double-table offsets
   int dW, dinvW, dTmid, dcp, dh, dg, dlnA, db, dTh, dtroe, deff, dexp, dnu, dcsrnu;
@@ -53,7 +54,7 @@ __device__ __forceinline__ int meta_neff(int w) { return (w >> 8) & 255; }
 __device__ __forceinline__ int meta_troe(int w) { return w >> 16; }
 
 struct MechView {
-  int ns, nr;
+  int ns, nr, ntroe, nfall;
   const double *W, *invW, *Tmid, *cp, *h, *gb, *lnA, *b, *Th, *troe, *eff, *etab;
   const double *dnu;      // per reaction: sum of product minus reactant coefficients
   const double *csrnu;    // per species -> reaction entry: the net coefficient nu
@@ -65,6 +66,8 @@ __device__ __forceinline__ MechView make_view(const MechLayout &L, const double 
   MechView v;
   v.ns = L.ns;
   v.nr = L.nr;
+  v.ntroe = L.ntroe;
+  v.nfall = L.nfall;
   v.W = d + L.dW;
   v.invW = d + L.dinvW;
   v.Tmid = d + L.dTmid;
@@ -120,51 +123,6 @@ __device__ __forceinline__ double poly_dcp(const double *c, double T) {
 }
 
 // ---------------------------------------------------------------------------
-// Troe falloff factor Pfac = Pr/(1+Pr) F, Pr = k0 [M] / k_inf, with its
-// logarithmic derivatives in T (at fixed [M]) and in [M].
-// ---------------------------------------------------------------------------
-struct TroeOut {
-  double P, dlnP_dT, dlnP_dM;
-};
-
-template <bool DERIV>
-__device__ __forceinline__ TroeOut troe_factor(const double *tp, double T, double logT,
-                                               double invT, double kinf, double dlnkinf,
-                                               double M) {
-  TroeOut o;
-  double k0 = exp(tp[0] + tp[1] * logT - tp[2] * invT);
-  double a = tp[3];
-  double e3 = exp(-T * tp[4]), e1 = exp(-T * tp[5]), e2 = exp(-tp[6] * invT);
-  double Fc = (1.0 - a) * e3 + a * e1 + e2;
-  double lFc = log10(Fc);
-  double Pr = k0 * M / kinf;
-  double L = log10(Pr);
-  double c = -0.4 - 0.67 * lFc, nn = 0.75 - 1.27 * lFc;
-  const double d = 0.14;
-  double u = L + c, v = nn - d * u;
-  double X = u / v;
-  double den = 1.0 + X * X;
-  double lF = lFc / den;
-  o.P = Pr / (1.0 + Pr) * exp(lF * LN10);
-  o.dlnP_dT = 0.0;
-  o.dlnP_dM = 0.0;
-  if (DERIV) {
-    double dFc = -(1.0 - a) * tp[4] * e3 - a * tp[5] * e1 + tp[6] * invT * invT * e2;
-    double dX_dL = nn / (v * v);
-    double dv = -1.27 + d * 0.67;
-    double dX_dlFc = (-0.67 * v - u * dv) / (v * v);
-    double dlF_dL = -lFc * 2.0 * X * dX_dL / (den * den);
-    double dlF_dlFc = 1.0 / den - lFc * 2.0 * X * dX_dlFc / (den * den);
-    double dlnk0 = tp[1] * invT + tp[2] * invT * invT;
-    double dL_dT = (dlnk0 - dlnkinf) / LN10;
-    double dlnP_dL = LN10 / (1.0 + Pr) + LN10 * dlF_dL;
-    o.dlnP_dT = dlnP_dL * dL_dT + dlF_dlFc * dFc / Fc;
-    o.dlnP_dM = dlnP_dL / (M * LN10);
-  }
-  return o;
-}
-
-// ---------------------------------------------------------------------------
 // Exponential for the rate expressions: Tang's table-driven method
 // (ACM TOMS 15, 1989).  exp(x) = 2^m 2^(j/128) exp(r) with N = round(128 x /
 // ln 2), j = N mod 128, m = N div 128, r = x - N ln2/128 (|r| <= ln2/256,
@@ -196,6 +154,51 @@ __device__ __forceinline__ double kexp(double x, const double *tab) {
   const double v = fma(tj, p, tj);
   const long long m = (long long)(N >> 7);     // floor division (arithmetic shift)
   return __longlong_as_double(__double_as_longlong(v) + (m << 52));
+}
+
+// ---------------------------------------------------------------------------
+// Troe falloff factor Pfac = Pr/(1+Pr) F, Pr = k0 [M] / k_inf, with its
+// logarithmic derivatives in T (at fixed [M]) and in [M].
+// ---------------------------------------------------------------------------
+struct TroeOut {
+  double P, dlnP_dT, dlnP_dM;
+};
+
+template <bool DERIV>
+__device__ __forceinline__ TroeOut troe_factor(const double *tp, double T, double logT,
+                                               double invT, double kinf, double dlnkinf,
+                                               double M, const double *etab) {
+  TroeOut o;
+  double k0 = kexp(tp[0] + tp[1] * logT - tp[2] * invT, etab);
+  double a = tp[3];
+  double e3 = kexp(-T * tp[4], etab), e1 = kexp(-T * tp[5], etab), e2 = kexp(-tp[6] * invT, etab);
+  double Fc = (1.0 - a) * e3 + a * e1 + e2;
+  double lFc = log10(Fc);
+  double Pr = k0 * M / kinf;
+  double L = log10(Pr);
+  double c = -0.4 - 0.67 * lFc, nn = 0.75 - 1.27 * lFc;
+  const double d = 0.14;
+  double u = L + c, v = nn - d * u;
+  double X = u / v;
+  double den = 1.0 + X * X;
+  double lF = lFc / den;
+  o.P = Pr / (1.0 + Pr) * kexp(lF * LN10, etab);
+  o.dlnP_dT = 0.0;
+  o.dlnP_dM = 0.0;
+  if (DERIV) {
+    double dFc = -(1.0 - a) * tp[4] * e3 - a * tp[5] * e1 + tp[6] * invT * invT * e2;
+    double dX_dL = nn / (v * v);
+    double dv = -1.27 + d * 0.67;
+    double dX_dlFc = (-0.67 * v - u * dv) / (v * v);
+    double dlF_dL = -lFc * 2.0 * X * dX_dL / (den * den);
+    double dlF_dlFc = 1.0 / den - lFc * 2.0 * X * dX_dlFc / (den * den);
+    double dlnk0 = tp[1] * invT + tp[2] * invT * invT;
+    double dL_dT = (dlnk0 - dlnkinf) / LN10;
+    double dlnP_dL = LN10 / (1.0 + Pr) + LN10 * dlF_dL;
+    o.dlnP_dT = dlnP_dL * dL_dT + dlF_dlFc * dFc / Fc;
+    o.dlnP_dM = dlnP_dL / (M * LN10);
+  }
+  return o;
 }
 
 // ---------------------------------------------------------------------------
@@ -308,8 +311,10 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
         phi = M;
         dphi_dM = 1.0;
       } else {
-        TroeOut t = troe_factor<true>(m.troe + NTROE * meta_troe(meta), T, logT, invT, kf,
-                                      dlnkf, M);
+        // the derivatives only when the Jacobian is assembled
+        const double *tp = m.troe + NTROE * meta_troe(meta);
+        TroeOut t = wantJ ? troe_factor<true>(tp, T, logT, invT, kf, dlnkf, M, m.etab)
+                          : troe_factor<false>(tp, T, logT, invT, kf, dlnkf, M, m.etab);
         phi = t.P;
         dphi_dT = t.P * t.dlnP_dT;
         dphi_dM = t.P * t.dlnP_dM;

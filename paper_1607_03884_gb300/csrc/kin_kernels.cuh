@@ -184,8 +184,19 @@ __global__ void KIN_THREAD_BOUNDS k_integrate_queue(KernelArgs a) {
 
 // WARP layout: one state per group of L lanes; groups pop states from the
 // atomic queue.
+// Register cap of the WARP kernels (0: the compiler's choice under the
+// 256-thread bound): a build-time tuning knob.
+#ifndef KIN_WARP_MAXNREG
+#define KIN_WARP_MAXNREG 0
+#endif
+#if KIN_WARP_MAXNREG > 0
+#define KIN_WARP_BOUNDS __maxnreg__(KIN_WARP_MAXNREG)
+#else
+#define KIN_WARP_BOUNDS __launch_bounds__(256)
+#endif
+
 template <int L, typename LT, bool FDJ>
-__global__ void __launch_bounds__(256) k_integrate_lanes(KernelArgs a) {
+__global__ void KIN_WARP_BOUNDS k_integrate_lanes(KernelArgs a) {
   using G = Grp<L>;
   constexpr int WR = G::WR;
   extern __shared__ double smem[];

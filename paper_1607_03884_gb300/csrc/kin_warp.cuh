@@ -28,6 +28,12 @@
 
 namespace kin {
 
+// Elementary reactions of the rate-only path two per lane per round (1) or
+// one (0): a build-time tuning knob.
+#ifndef KIN_WARP_PAIRED_RATES
+#define KIN_WARP_PAIRED_RATES 0
+#endif
+
 template <int L>
 struct Grp {
   static_assert(L == 4 || L == 8 || L == 16 || L == 32, "lanes per state");
@@ -161,6 +167,66 @@ __device__ WarpBuf<LT> carve_warp_buf(char *p, int N, int nr, LT *Jglobal) {
   return w;
 }
 
+// Net rate kf prod C' - kr prod C'' of an elementary reaction i (no collider,
+// no falloff): straight-line code (the slot loops are unrolled and
+// predicated), so two calls on different reactions interleave as
+// independent FP64 chains.
+__device__ __forceinline__ double elem_rate(const MechView &m, const double *C,
+                                            const double *g, int i, double logT, double invT,
+                                            double lnPf) {
+  const int meta = m.meta[i];
+  const int *sl = m.slot + 6 * i;
+  const int nre = meta_nreac(meta), npr = meta_nprod(meta);
+  const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
+  double lnKc = m.dnu[i] * lnPf, fwd = 1.0, rev = 1.0;
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+    if (s < nre) {
+      const int sp = sl[s];
+      lnKc -= g[sp];
+      fwd *= C[sp];
+    }
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+    if (s < npr) {
+      const int sp = sl[3 + s];
+      lnKc += g[sp];
+      rev *= C[sp];
+    }
+  const double kr = kf * kexp(-lnKc, m.etab);
+  return kf * fwd - kr * rev;
+}
+
+// Net rate of a third-body or Troe falloff reaction i, without derivatives.
+__device__ __forceinline__ double falloff_rate(const MechView &m, const double *C,
+                                               const double *g, int i, double T, double logT,
+                                               double invT, double lnPf, double Ctot) {
+  const int meta = m.meta[i];
+  const int *sl = m.slot + 6 * i;
+  const int nre = meta_nreac(meta), npr = meta_nprod(meta);
+  const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
+  double lnKc = m.dnu[i] * lnPf, fwd = 1.0, rev = 1.0;
+  for (int s = 0; s < nre; ++s) {
+    lnKc -= g[sl[s]];
+    fwd *= C[sl[s]];
+  }
+  for (int s = 0; s < npr; ++s) {
+    lnKc += g[sl[3 + s]];
+    rev *= C[sl[3 + s]];
+  }
+  const double kr = kf * kexp(-lnKc, m.etab);
+  double M = Ctot;
+  const int e0 = m.eff0[i], ne = meta_neff(meta);
+  for (int e = 0; e < ne; ++e) M += m.eff[e0 + e] * C[m.effsp[e0 + e]];
+  double phi = M;
+  if (meta_type(meta) == 2) {
+    const double dlnkf = m.b[i] * invT + m.Th[i] * invT * invT;
+    phi = troe_factor<false>(m.troe + NTROE * meta_troe(meta), T, logT, invT, kf, dlnkf, M,
+                             m.etab).P;
+  }
+  return phi * (kf * fwd - kr * rev);
+}
+
 // ---------------------------------------------------------------------------
 // Source terms (and optionally the analytical Jacobian) for the group's state.
 // Same formulas as chem_eval (kin_device.cuh); returns 0 or 4 (non-finite).
@@ -224,7 +290,34 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
   G::sync();
   const double Ctot = rho * S;
   const double lnPf = 2.5003366899611787 - logT;  // ln(Patm / Ru) - ln T
-  for (int i0 = 0; i0 < m.nr; i0 += L) {
+  // Rates only (most evaluations: Newton stages, error refinement): the
+  // falloff reactions, which the device order puts first, in their own
+  // rounds (Troe, then third-body), so their branches never split a round of
+  // elementary reactions; then the elementary reactions two per lane per
+  // round, for two independent FP64 chains per lane.
+  if (!wantJ) {
+    for (int i0 = 0; i0 < m.ntroe; i0 += L)
+      if (i0 + lane < m.ntroe)
+        b.q[i0 + lane] = falloff_rate(m, b.C, b.g, i0 + lane, T, logT, invT, lnPf, Ctot);
+    for (int i0 = m.ntroe; i0 < m.nfall; i0 += L)
+      if (i0 + lane < m.nfall)
+        b.q[i0 + lane] = falloff_rate(m, b.C, b.g, i0 + lane, T, logT, invT, lnPf, Ctot);
+#if KIN_WARP_PAIRED_RATES
+    for (int i0 = m.nfall; i0 < m.nr; i0 += 2 * L) {
+      const int ia = i0 + lane, ib = i0 + L + lane;
+      const int ca = ia < m.nr ? ia : m.nr - 1, cb = ib < m.nr ? ib : m.nr - 1;
+      const double qa = elem_rate(m, b.C, b.g, ca, logT, invT, lnPf);
+      const double qb = elem_rate(m, b.C, b.g, cb, logT, invT, lnPf);
+      if (ia < m.nr) b.q[ia] = qa;
+      if (ib < m.nr) b.q[ib] = qb;
+    }
+#else
+    for (int i0 = m.nfall; i0 < m.nr; i0 += L)
+      if (i0 + lane < m.nr) b.q[i0 + lane] = elem_rate(m, b.C, b.g, i0 + lane, logT, invT, lnPf);
+#endif
+  }
+  const int nr_with_jac = wantJ ? m.nr : 0;
+  for (int i0 = 0; i0 < nr_with_jac; i0 += L) {
     const int i = i0 + lane;
     if (i >= m.nr) continue;
     const int meta = m.meta[i];
@@ -252,8 +345,9 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
         phi = M;
         dphi_dM = 1.0;
       } else {
-        TroeOut t = troe_factor<true>(m.troe + NTROE * meta_troe(meta), T, logT, invT, kf,
-                                      dlnkf, M);
+        const double *tp = m.troe + NTROE * meta_troe(meta);
+        TroeOut t = wantJ ? troe_factor<true>(tp, T, logT, invT, kf, dlnkf, M, m.etab)
+                          : troe_factor<false>(tp, T, logT, invT, kf, dlnkf, M, m.etab);
         phi = t.P;
         dphi_dT = t.P * t.dlnP_dT;
         dphi_dM = t.P * t.dlnP_dM;
