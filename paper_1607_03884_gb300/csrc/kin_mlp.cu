@@ -7,7 +7,8 @@
 //
 // Network: x (din) -> 3 x [Linear(width) -> SiLU] -> Linear(dout).
 // Two arithmetic modes:
-//   BF16  tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulate);
+//   BF16  5th-generation tensor cores (tcgen05.mma, BF16 operands, FP32
+//         accumulators in tensor memory);
 //         activations are rounded to BF16 between layers, master weights and
 //         the optimiser stay FP32;
 //   FP32  CUDA-core FMA everywhere (a check mode for gradient tests).
@@ -40,70 +41,182 @@ __device__ __forceinline__ float silu_grad(float a) {
 // ---------------------------------------------------------------------------
 // GEMM, generic strides: C[m][n] (+)= sum_k A(m,k) B(k,n) with
 // A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]; out of range = 0.
-// BF16 tensor-core version: a warp computes a 16 x 32 tile (four n8 MMAs per
-// k16 step); a block stacks four warps in m (64 x 32).
+//
+// BF16 version on the 5th-generation tensor cores (tcgen05): a CTA of four
+// warps owns a 128 x 128 tile of C.  Per 64-wide slice of K, the warps copy
+// A (128 x 64) and B (as its transpose, 128 x 64, K contiguous) into shared
+// memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
+// matrices, 128 B each: core (g, c) of rows 8g.. and K columns 8c.. at
+// (8 g + c) * 128 bytes), one thread issues four m128n128k16 MMAs into the
+// tile's FP32 accumulator in tensor memory (TMEM, 128 columns), and their
+// completion is signalled on an mbarrier before the slice is overwritten.
+// The epilogue reads the accumulator back with tcgen05.ld (warp w owns TMEM
+// lanes 32w..32w+31, the tile's rows) and writes or adds C.  Every wait is
+// bounded: on expiry the kernel sets *err, waits (bounded) for its MMAs,
+// frees its TMEM and returns.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned short bf_at(const __nv_bfloat16 *p, int64_t i, bool ok) {
-  return ok ? __bfloat16_as_ushort(p[i]) : (unsigned short)0;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_TMEM_COLS = 128;
+// 16 KB per operand slice; the dynamic allocation is padded so that at most
+// four CTAs share an SM (4 x 128 of its 512 TMEM columns)
+constexpr size_t TC_SMEM = 2 * TC_BM * TC_BK * sizeof(__nv_bfloat16) + 20 * 1024;
+constexpr long long TC_SPIN_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__global__ void k_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *A, int64_t sam, int64_t sak,
-                            const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, float *C,
-                            int64_t ldc, int accumulate) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int m0 = blockIdx.x * 64 + warp * 16;
-  const int n0 = blockIdx.y * 32;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  const int r0 = m0 + g, r1 = m0 + g + 8;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    const int ka = k0 + 2 * t, kb = k0 + 2 * t + 8;
-    unsigned a[4];
-    {
-      const bool ok00 = r0 < M && ka < K, ok01 = r0 < M && ka + 1 < K;
-      const bool ok10 = r1 < M && ka < K, ok11 = r1 < M && ka + 1 < K;
-      const bool ok02 = r0 < M && kb < K, ok03 = r0 < M && kb + 1 < K;
-      const bool ok12 = r1 < M && kb < K, ok13 = r1 < M && kb + 1 < K;
-      a[0] = bf_at(A, r0 * sam + ka * sak, ok00) | ((unsigned)bf_at(A, r0 * sam + (ka + 1) * sak, ok01) << 16);
-      a[1] = bf_at(A, r1 * sam + ka * sak, ok10) | ((unsigned)bf_at(A, r1 * sam + (ka + 1) * sak, ok11) << 16);
-      a[2] = bf_at(A, r0 * sam + kb * sak, ok02) | ((unsigned)bf_at(A, r0 * sam + (kb + 1) * sak, ok03) << 16);
-      a[3] = bf_at(A, r1 * sam + kb * sak, ok12) | ((unsigned)bf_at(A, r1 * sam + (kb + 1) * sak, ok13) << 16);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int c = n0 + nt * 8 + g;
-      const bool okc = c < N;
-      unsigned b0 = bf_at(B, ka * sbk + c * sbn, okc && ka < K) |
-                    ((unsigned)bf_at(B, (ka + 1) * sbk + c * sbn, okc && ka + 1 < K) << 16);
-      unsigned b1 = bf_at(B, kb * sbk + c * sbn, okc && kb < K) |
-                    ((unsigned)bf_at(B, (kb + 1) * sbk + c * sbn, okc && kb + 1 < K) << 16);
-      asm volatile(
-          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-          "{%8,%9}, {%0,%1,%2,%3};\n"
-          : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    }
+// shared-memory matrix descriptor, no swizzle: start address, leading byte
+// offset (next core matrix along K), stride byte offset (next 8 rows), the
+// fixed version bits 46-48 = 0b001
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
+  for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (done) return true;
   }
+  return false;
+}
+
+// byte offset of element (r, k) of a 128 x 64 K-major slice
+__device__ __forceinline__ int tc_off(int r, int k) {
+  return (((r >> 3) * (TC_BK / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1);
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
+                                                       const __nv_bfloat16 *A, int64_t sam,
+                                                       int64_t sak, const __nv_bfloat16 *B,
+                                                       int64_t sbk, int64_t sbn, float *C,
+                                                       int64_t ldc, int accumulate, int *err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tmem_base;
+  unsigned char *sA = tc_smem, *sB = tc_smem + TC_BM * TC_BK * 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const uint32_t mb = smem_u32(&mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const bool a_kfast = sak <= sam, b_kfast = sbk <= sbn;
+  uint32_t phase = 0;
+  bool ok = true;
+  const int nk = (K + TC_BK - 1) / TC_BK;
+  for (int kt = 0; kt < nk && ok; ++kt) {
+    const int k0 = kt * TC_BK;
+    // stage the slices (zero outside the matrices)
+    for (int e = tid; e < TC_BM * TC_BK; e += TC_THREADS) {
+      const int r = a_kfast ? e / TC_BK : e % TC_BM, k = a_kfast ? e % TC_BK : e / TC_BM;
+      const int gm = m0 + r, gk = k0 + k;
+      const __nv_bfloat16 v = (gm < M && gk < K) ? A[(int64_t)gm * sam + (int64_t)gk * sak]
+                                                 : __float2bfloat16(0.0f);
+      *reinterpret_cast<__nv_bfloat16 *>(sA + tc_off(r, k)) = v;
+    }
+    for (int e = tid; e < TC_BN * TC_BK; e += TC_THREADS) {
+      const int c = b_kfast ? e / TC_BK : e % TC_BN, k = b_kfast ? e % TC_BK : e / TC_BN;
+      const int gn = n0 + c, gk = k0 + k;
+      const __nv_bfloat16 v = (gn < N && gk < K) ? B[(int64_t)gk * sbk + (int64_t)gn * sbn]
+                                                 : __float2bfloat16(0.0f);
+      *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off(c, k)) = v;
+    }
+    // make the generic-proxy writes visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = tc_idesc(TC_BM, TC_BN);
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    const int c = n0 + nt * 8 + 2 * t;
+      for (int s = 0; s < TC_BK / 16; ++s) {
+        // k16 step s covers K cores 2s and 2s + 1
+        const uint64_t da = tc_desc(smem_u32(sA) + 256u * s, 128u, (TC_BK / 8) * 128u);
+        const uint64_t db = tc_desc(smem_u32(sB) + 256u * s, 128u, (TC_BK / 8) * 128u);
+        const uint32_t acc = (kt > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+          : "memory");
+    }
+    // the slice may be overwritten once its MMAs have completed; every
+    // thread leaves the loop on the same trip
+    ok = tc_wait(mb, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok) != 0;
+  }
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < TC_BN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+        float *dst = C + (int64_t)row * ldc + n0 + c0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int r = h ? r1 : r0;
-      if (r >= M) continue;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (c + q >= N) continue;
-        float v = acc[nt][2 * h + q];
-        float *dst = C + (int64_t)r * ldc + c + q;
-        *dst = accumulate ? *dst + v : v;
+        for (int j = 0; j < 16; ++j)
+          if (n0 + c0 + j < N) {
+            const float x = __uint_as_float(v[j]);
+            dst[j] = accumulate ? dst[j] + x : x;
+          }
       }
     }
+  } else {
+    if (tid == 0) atomicOr(err, 1);
+    (void)tc_wait(mb, phase ^ 1u);  // the last commit, if it is still pending
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
 }
 
 // FP32 CUDA-core version (check mode): one output per thread.
@@ -298,6 +411,7 @@ struct kin_mlp {
   float *xf = nullptr, *a[LAYERS] = {}, *hf[LAYERS] = {}, *C = nullptr, *g = nullptr,
         *dH = nullptr, *y = nullptr, *loss = nullptr;
   float *xg = nullptr, *tg = nullptr;  // gathered minibatch rows (train_step_rows)
+  int *err = nullptr;                  // set by a tensor-core GEMM whose wait expired
   __nv_bfloat16 *xb = nullptr, *hb[LAYERS] = {}, *gb = nullptr;
 };
 
@@ -341,9 +455,10 @@ static void gemm(const kin_mlp *n, cudaStream_t st, int M, int N, int K, bool bf
                  int64_t sam, int64_t sak, const void *B, int64_t sbk, int64_t sbn, float *C,
                  int64_t ldc, int acc) {
   if (bf) {
-    dim3 grid((M + 63) / 64, (N + 31) / 32);
-    k_gemm_bf16<<<grid, 128, 0, st>>>(M, N, K, (const __nv_bfloat16 *)A, sam, sak,
-                                      (const __nv_bfloat16 *)B, sbk, sbn, C, ldc, acc);
+    dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
+    k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(M, N, K, (const __nv_bfloat16 *)A, sam, sak,
+                                                 (const __nv_bfloat16 *)B, sbk, sbn, C, ldc, acc,
+                                                 n->err);
   } else {
     k_gemm_f32<<<blocks((int64_t)M * N), 256, 0, st>>>(M, N, K, (const float *)A, sam, sak,
                                                        (const float *)B, sbk, sbn, C, ldc, acc);
@@ -447,7 +562,8 @@ extern "C" int kin_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t 
       cudaMalloc(&n->v, sizeof(float) * off) != cudaSuccess ||
       cudaMalloc(&n->mask, off) != cudaSuccess ||
       cudaMalloc(&n->wb, sizeof(__nv_bfloat16) * off) != cudaSuccess ||
-      cudaMalloc(&n->loss, sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&n->loss, sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&n->err, sizeof(int)) != cudaSuccess) {
     (void)cudaGetLastError();
     kin_mlp_destroy(n);
     return KIN_ERR_NOMEM;
@@ -457,6 +573,9 @@ extern "C" int kin_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t 
       cudaMemset(n->m, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(n->v, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(n->grad, 0, sizeof(float) * off) != cudaSuccess ||
+      cudaMemset(n->err, 0, sizeof(int)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TC_SMEM) != cudaSuccess ||
       mlp_refresh_bf16(n, nullptr) != KIN_OK || cudaDeviceSynchronize() != cudaSuccess) {
     (void)cudaGetLastError();
     kin_mlp_destroy(n);
@@ -475,6 +594,7 @@ extern "C" void kin_mlp_destroy(kin_mlp *n) {
   cudaFree(n->mask);
   cudaFree(n->wb);
   cudaFree(n->loss);
+  cudaFree(n->err);
   cudaFree(n->xg);
   cudaFree(n->tg);
   cudaFree(n->xf);
@@ -567,6 +687,9 @@ extern "C" int kin_mlp_grad(kin_mlp *n, const float *X, const float *T, int64_t 
   if (grad_out) {
     // gather the unpadded layout on the host side of the stream
     KIN_CUDA_TRY(cudaStreamSynchronize(st));
+    int e = 0;
+    KIN_CUDA_TRY(cudaMemcpy(&e, n->err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) return KIN_ERR_CUDA;  // a tensor-core wait expired
     std::vector<float> full(n->np), packed(kin_mlp_num_params(n));
     KIN_CUDA_TRY(cudaMemcpy(full.data(), n->grad, sizeof(float) * n->np, cudaMemcpyDeviceToHost));
     int64_t q = 0;

@@ -39,7 +39,12 @@ def bf16(x):
 
 
 U_BF16 = 2.0 ** -8      # a BF16 rounding flip moves a value by at most 2^-8 of it
-U_ACC = 2.0 ** -20      # FP32 accumulation and __expf, relative to the absolute terms
+
+
+def U_ACC(K):
+    """FP32 accumulation of K products (the standard K u bound, u = 2^-24), plus
+    the fast exponential of SiLU, relative to the sum of the absolute terms."""
+    return (K + 4) * 2.0 ** -24
 
 
 def bf16_bounds(W, b, cache, y, t):
@@ -56,7 +61,7 @@ def bf16_bounds(W, b, cache, y, t):
     Eh = np.zeros_like(h[0])                                   # the input is rounded alike
     EC = []
     for l in range(L):
-        E = Eh @ aW[l] + U_ACC * (np.abs(h[l]) @ aW[l])
+        E = Eh @ aW[l] + U_ACC(W[l].shape[0]) * (np.abs(h[l]) @ aW[l])
         EC.append(E)
         if l < L - 1:
             Eh = 1.1 * E + U_BF16 * np.abs(h[l + 1])
@@ -72,11 +77,12 @@ def bf16_bounds(W, b, cache, y, t):
             Eg = Eg * sg + np.abs(g) * 0.5 * EC[l]
             g = g * M.silu_grad(a[l])
         Egr = Eg + U_BF16 * np.abs(g)
+        nb = h[l].shape[0]
         EW[l] = (hin_err[l].T @ np.abs(g) + np.abs(h[l]).T @ Egr
-                 + U_ACC * (np.abs(h[l]).T @ np.abs(g)))
-        Eb[l] = Eg.sum(axis=0) + U_ACC * np.abs(g).sum(axis=0)
+                 + U_ACC(nb) * (np.abs(h[l]).T @ np.abs(g)))
+        Eb[l] = Eg.sum(axis=0) + U_ACC(nb) * np.abs(g).sum(axis=0)
         dH = g @ W[l].T
-        Eg = Egr @ aW[l].T + U_ACC * (np.abs(g) @ aW[l].T)
+        Eg = Egr @ aW[l].T + U_ACC(W[l].shape[1]) * (np.abs(g) @ aW[l].T)
         g = dH
     return Ey, EW, Eb
 
@@ -277,14 +283,18 @@ def test_prediction_matches_the_reference_network():
 
 def test_trained_predictor_removes_steps_at_equal_error():
     """What the learned part gains: a predictor trained on integrator-made
-    targets (CH4-like states, WARP layout, FP32 matrices) gives a first step
-    that removes steps against the starting-step heuristic, and the results
-    stay as close to the exact solution (oracle at rtol 1e-13) as without it."""
+    targets (2^17 CH4-like states, WARP layout, FP32 matrices) supplies the
+    first internal step of 2^14 fresh states at dt = 1e-4 s.  Radau's error
+    test still judges every step.  It must remove at least 1.5 % of the steps
+    while the results stay as accurate: against a tight reference (the
+    oracle at rtol 1e-10, atol 1e-17) on 48 sampled states, the largest
+    E_i (Sec. 2.3) at most 1.5 times and the median at most 1.2 times the
+    run without it."""
     from oracle import oracle as O
     from paper_1607_03884_gb300 import learned
     mech = synth.make_mechanism("ch4")
     tr = synth.make_states(mech, 1 << 17, seed=47, T_range=(800.0, 2600.0))
-    te = synth.make_states(mech, 1 << 12, seed=46, T_range=(800.0, 2600.0))
+    te = synth.make_states(mech, 1 << 14, seed=46, T_range=(800.0, 2600.0))
     mg = kin.Mechanism(mech)
     dt = 1e-4
     pred, info = learned.train(mech, mg, tr, dt, width=256, epochs=8, batch=1024, layout="warp")
@@ -302,16 +312,19 @@ def test_trained_predictor_removes_steps_at_equal_error():
         runs[tag] = (Yw.cpu().numpy(), Tw.cpu().numpy(), mg.stats())
     s0, s1 = runs["none"][2], runs["predicted"][2]
     assert s0["failed"] == 0 and s1["failed"] == 0
-    assert s1["nstep"] < 0.985 * s0["nstep"], (s1["nstep"], s0["nstep"])
-    idx = np.arange(0, te.n, te.n // 16)
-    Yx, Tx, _ = O.integrate(mech, te.subset(idx), dt, rtol=1e-13, atol=1e-20)
+    idx = np.arange(0, te.n, te.n // 48)
+    Yx, Tx, _ = O.integrate(mech, te.subset(idx), dt, rtol=1e-10, atol=1e-17,
+                            transform_tol=False)
     yx = np.concatenate([Tx[None], Yx[:-1]])
     E = {tag: O.error_norm(np.concatenate([r[1][idx][None], r[0][:-1, idx]]), yx)
          for tag, r in runs.items()}
-    print(f"\nsteps/state {s0['nstep'] / te.n:.2f} -> {s1['nstep'] / te.n:.2f}; "
-          f"E vs exact max {E['none'].max():.3g} -> {E['predicted'].max():.3g}")
-    assert E["predicted"].max() <= max(10.0 * E["none"].max(), 30.0)
-    assert np.median(E["predicted"]) <= max(3.0 * np.median(E["none"]), 1.0)
+    print(f"\nsteps/state {s0['nstep'] / te.n:.2f} -> {s1['nstep'] / te.n:.2f}, right-hand "
+          f"sides {s0['nfcn'] / te.n:.1f} -> {s1['nfcn'] / te.n:.1f}; E vs exact max "
+          f"{E['none'].max():.3g} -> {E['predicted'].max():.3g}, median "
+          f"{np.median(E['none']):.3g} -> {np.median(E['predicted']):.3g}")
+    assert s1["nstep"] < 0.985 * s0["nstep"], (s1["nstep"], s0["nstep"])
+    assert E["predicted"].max() <= 1.5 * E["none"].max()
+    assert np.median(E["predicted"]) <= 1.2 * np.median(E["none"])
 
 
 def test_train_step_on_gathered_rows_matches_the_plain_step():
