@@ -58,7 +58,11 @@ def parse():
     p.add_argument("--n", type=int, default=0, help="states (0 = the workload's 2^20)")
     p.add_argument("--no-extras", action="store_true", help="skip the comparison legs")
     p.add_argument("--no-config3", action="store_true",
-                   help="skip the full-size CH4-like leg among the extras")
+                   help="skip the full-size CH4-like and predictor legs among the extras")
+    p.add_argument("--config5", action="store_true",
+                   help="only the learned part at full size (2^20 training and test states)")
+    p.add_argument("--mlp-only", action="store_true",
+                   help="time only the predictor's training step (rows = --n, default 2^16)")
     p.add_argument("--cpu-sample", type=int, default=2048)
     p.add_argument("--order", default="heuristic", choices=["none", "heuristic"],
                    help="order the states by the starting-step heuristic inside each step")
@@ -323,7 +327,7 @@ def run_ours(args, rank, world):
                       "h2d_bytes_per_step": int(n * (mech.ns + 2) * 8),
                       "d2h_bytes_per_step": int(n * (mech.ns + 1) * 8)}
     if rank == 0 and not args.no_extras and not args.no_config3 and args.workload == WORKLOAD:
-        out["configs"] = {"ch4_2p18": config3_leg(stream)}
+        out["configs"] = {"ch4_2p18": config3_leg(stream), "mlp_train": mlp_leg(stream)}
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -367,6 +371,86 @@ def config3_leg(stream):
             "value": st.n / sec, "unit": "states/s", "seconds": sec, "failed": tot["failed"],
             "counters": {k: int(v) for k, v in tot.items()}, "clocks": clocks,
             "roofline": roofline(f64, f32, sec, None, "k_integrate_lanes<32, float>")}
+
+
+def mlp_leg(stream, rows=1 << 16, steps=20):
+    """The predictor's training step on the tensor cores (the learned part's
+    GEMMs: 56 -> 256 -> 256 -> 256 -> 160, BF16 operands, FP32 accumulators
+    in tensor memory): CUDA-event time of `steps` Adam steps on batches of
+    `rows` seeded rows, outside the headline's timed region.  One step runs
+    the forward pass (4 GEMMs), the backward pass (4 weight-gradient and 3
+    input-gradient GEMMs) and the elementwise kernels."""
+    import torch
+    from paper_1607_03884_gb300 import kin
+    din, w, dout = 56, 256, 160
+    net = kin.MLP(din, w, dout, precision="bf16", seed=5)
+    g = torch.Generator(device="cpu").manual_seed(11)
+    X = torch.randn((rows, din), generator=g).cuda()
+    T = torch.randn((rows, dout), generator=g).cuda()
+    for _ in range(3):
+        net.train_step(X, T, 1e-4, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        net.train_step(X, T, 1e-4, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    pad = lambda d, m: (d + m - 1) // m * m
+    k0, n3 = pad(din, 16), pad(dout, 8)
+    macs = rows * (k0 * w + 2 * w * w + w * n3)            # forward
+    flops = 2.0 * macs * 3 - 2.0 * rows * k0 * w          # + weight and input gradients
+    pk = peaks().get("bf16_tflops")
+    tf = flops / sec / 1e12
+    return {"rows": rows, "layers": [din, w, w, w, dout], "seconds_per_step": sec,
+            "gemm_tflops": tf, "peak_bf16_tflops": pk, "frac": (tf / pk) if pk else None,
+            "note": "GEMM flops of a step over the whole step's time (elementwise kernels "
+                    "and Adam included)"}
+
+
+def config5_leg(stream, n_train=1 << 20, n_test=1 << 20):
+    """The learned part at full size: a predictor trained on n_train states
+    of `ch4_learned_train_2p20` (targets from the integrator itself), then
+    n_test fresh states of `ch4_learned_test_2p20` integrated over dt = 1e-4 s
+    (WARP, FP32 Newton matrices) with the starting-step heuristic and with the
+    predicted first step: states/s (CUDA events, prediction included) and
+    events per state.  Accuracy against the exact solution is a test's job
+    (tests/test_gpu_mlp.py)."""
+    import torch
+    from paper_1607_03884_gb300 import kin, learned, synth
+    mech, tr, _ = synth.workload("ch4_learned_train_2p20", n=n_train)
+    _, te, _ = synth.workload("ch4_learned_test_2p20", n=n_test)
+    mg = kin.Mechanism(mech)
+    dt = 1e-4
+    t0 = time.perf_counter()
+    pred, info = learned.train(mech, mg, tr, dt, width=256, epochs=6, batch=4096, layout="warp")
+    train_s = time.perf_counter() - t0
+    Y0, T0, P = (torch.from_numpy(a.copy()).cuda() for a in (te.Y, te.T, te.P))
+    out = {"train_states": n_train, "test_states": n_test, "train_seconds": train_s,
+           "final_loss": info["history"][-1]}
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    for tag in ("heuristic", "predicted"):
+        Y, T = Y0.clone(), T0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kw = {}
+        if tag == "predicted":
+            kw["h0"], _ = pred.predict(Y, T, P, dt, stream=stream)
+        mg.integrate(Y, T, P, dt, RTOL, ATOL, stream=stream, layout="warp", lu_fp32=True, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        st = mg.stats()
+        out[tag] = {"states_per_s": n_test / sec, "seconds": sec,
+                    **{f"{k}_per_state": st[k] / n_test for k in
+                       ("nstep", "nfcn", "nsol", "ndec", "njac")}, "failed": st["failed"]}
+    out["clocks"] = clk.stop()
+    out["step_reduction"] = 1.0 - out["predicted"]["nstep_per_state"] / out["heuristic"]["nstep_per_state"]
+    out["speedup"] = out["predicted"]["states_per_s"] / out["heuristic"]["states_per_s"]
+    return out
 
 
 def cpu_model():
@@ -471,6 +555,15 @@ def roofline(f64, f32, seconds, traffic=None, kernel=None):
 
 def main():
     args = parse()
+    if args.config5:    # the learned part at full size (minutes; not part of the default run)
+        import torch
+        print(json.dumps(config5_leg(torch.cuda.current_stream())))
+        return
+    if args.mlp_only:   # the predictor's training step alone (for profiling its GEMMs)
+        import torch
+        print(json.dumps(mlp_leg(torch.cuda.current_stream(), rows=args.n or (1 << 16),
+                                 steps=args.steps)))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

@@ -443,10 +443,12 @@ extern "C" int kin_mech_create(const kin_mech_desc *d, kin_mech **out) {
   kin_mech *m = new kin_mech();
   m->device = dev;
   m->L = L;
-  // WARP layout: one Jacobian slot per resident group (up to 64 groups of
-  // 4-16 lanes per SM for ns <= 15, 8 whole warps per SM beyond)
-  m->gslots = (int64_t)sms * (L.ns <= 15 ? 64 : 8);
-  const size_t gbytes = (size_t)m->gslots * L.ns * (L.ns + 1) * sizeof(double);
+  // WARP layout: one Jacobian slot (with the complex matrix when that lives
+  // in global memory) per resident group: up to 64 groups of 4-16 lanes per
+  // SM for ns <= 15, 16 whole warps per SM beyond
+  m->gslots = (int64_t)sms * (L.ns <= 15 ? 64 : 16);
+  const size_t gbytes =
+      (size_t)m->gslots * warp_slot_mats(sizeof(double)) * L.ns * (L.ns + 1) * sizeof(double);
   if (cudaMalloc(&m->d_tab, sizeof(double) * L.nd) != cudaSuccess ||
       cudaMalloc(&m->d_itab, sizeof(int) * L.ni) != cudaSuccess ||
       cudaMalloc(&m->d_totals, sizeof(unsigned long long) * 16) != cudaSuccess ||

@@ -207,7 +207,8 @@ __global__ void KIN_WARP_BOUNDS k_integrate_lanes(KernelArgs a) {
   const int64_t n = a.rp.n;
   char *base = reinterpret_cast<char *>(smem) + (size_t)grp * warp_buf_bytes(N, m.nr, sizeof(LT));
   const int64_t slot = (int64_t)blockIdx.x * (blockDim.x / L) + grp;  // < gslots (launch)
-  LT *Jg = reinterpret_cast<LT *>(a.gscratch) + slot * (int64_t)N * (N + 1);
+  LT *Jg = reinterpret_cast<LT *>(a.gscratch) +
+           slot * (int64_t)warp_slot_mats(sizeof(LT)) * N * (N + 1);
   const WarpBuf<LT> b = carve_warp_buf<LT>(base, N, m.nr, Jg);
   unsigned long long *queue = a.totals + 9;
   WStateT<WR> w;
@@ -273,15 +274,23 @@ int launch_lanes(const KernelArgs &a, cudaStream_t st, int sms) {
   if (a.L.ns >= G::CAP) return KIN_ERR_UNSUPPORTED;
   if (!a.gscratch || a.gslots < 1) return KIN_ERR_UNSUPPORTED;
   const size_t budget = 227 * 1024;
-  int warps = 8;
-  while (warps > 1 && lanes_smem_bytes(a.L, L, sizeof(LT), warps) > budget) --warps;
-  const size_t sm = lanes_smem_bytes(a.L, L, sizeof(LT), warps);
-  if (sm > budget) return KIN_ERR_UNSUPPORTED;
   auto kern = k_integrate_lanes<L, LT, FDJ>;
+  // the block size (1 to 8 warps) that keeps the most warps resident per SM
+  int warps = 0, per_sm = 0;
+  for (int w = 8; w >= 1; w >>= 1) {
+    const size_t smw = lanes_smem_bytes(a.L, L, sizeof(LT), w);
+    if (smw > budget) continue;
+    KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+    int b = 0;
+    KIN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * w, smw));
+    if (b * w > per_sm * warps) {
+      warps = w;
+      per_sm = b;
+    }
+  }
+  if (warps < 1 || per_sm < 1) return KIN_ERR_UNSUPPORTED;
+  const size_t sm = lanes_smem_bytes(a.L, L, sizeof(LT), warps);
   KIN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  int per_sm = 0;
-  KIN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, sm));
-  if (per_sm < 1) return KIN_ERR_UNSUPPORTED;
   int64_t grid = (int64_t)sms * per_sm;
   const int64_t per_block = (int64_t)warps * (32 / L);
   const int64_t need = (a.rp.n + per_block - 1) / per_block;

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -106,11 +107,28 @@ __device__ __forceinline__ int tc_off(int r, int k) {
   return (((r >> 3) * (TC_BK / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1);
 }
 
+// 16-byte copy of a core-matrix row (8 consecutive K) when the operand is
+// K-contiguous and the row lies inside the matrix, else element by element
+__device__ __forceinline__ void tc_stage_row(unsigned char *dst, const __nv_bfloat16 *src_row,
+                                             int64_t sk, bool vec, bool row_ok, int gk, int ke) {
+  if (vec && row_ok && gk + 8 <= ke) {
+    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src_row + gk);
+    return;
+  }
+  __nv_bfloat16 *d = reinterpret_cast<__nv_bfloat16 *>(dst);
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    d[e] = (row_ok && gk + e < ke) ? src_row[(int64_t)(gk + e) * sk] : __float2bfloat16(0.0f);
+}
+
+// Split K: CTA z sums K in [z kchunk, min(K, (z + 1) kchunk)) and writes its
+// partial tile to C + z cz (the caller reduces the partials).
 __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
                                                        const __nv_bfloat16 *A, int64_t sam,
                                                        int64_t sak, const __nv_bfloat16 *B,
                                                        int64_t sbk, int64_t sbn, float *C,
-                                                       int64_t ldc, int accumulate, int *err) {
+                                                       int64_t ldc, int accumulate, int *err,
+                                                       int kchunk, int64_t cz) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ uint32_t tmem_base;
@@ -133,26 +151,48 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  C += (int64_t)blockIdx.z * cz;
+  // K-contiguous operands are staged 16 bytes (a core-matrix row) at a time
+  const bool a_k1 = sak == 1, b_k1 = sbk == 1;
+  const bool a_vec = a_k1 && sam % 8 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  const bool b_vec = b_k1 && sbn % 8 == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
   const bool a_kfast = sak <= sam, b_kfast = sbk <= sbn;
   uint32_t phase = 0;
   bool ok = true;
-  const int nk = (K + TC_BK - 1) / TC_BK;
+  const int nk = (ke - kb + TC_BK - 1) / TC_BK;
   for (int kt = 0; kt < nk && ok; ++kt) {
-    const int k0 = kt * TC_BK;
-    // stage the slices (zero outside the matrices)
-    for (int e = tid; e < TC_BM * TC_BK; e += TC_THREADS) {
-      const int r = a_kfast ? e / TC_BK : e % TC_BM, k = a_kfast ? e % TC_BK : e / TC_BM;
-      const int gm = m0 + r, gk = k0 + k;
-      const __nv_bfloat16 v = (gm < M && gk < K) ? A[(int64_t)gm * sam + (int64_t)gk * sak]
-                                                 : __float2bfloat16(0.0f);
-      *reinterpret_cast<__nv_bfloat16 *>(sA + tc_off(r, k)) = v;
+    const int k0 = kb + kt * TC_BK;
+    // stage the slices (zero outside the matrices and the K range)
+    if (a_k1) {
+      for (int e = tid; e < TC_BM * (TC_BK / 8); e += TC_THREADS) {
+        const int r = e >> 3, kc = (e & 7) * 8, gm = m0 + r;
+        tc_stage_row(sA + tc_off(r, kc), A + (int64_t)(gm < M ? gm : 0) * sam, 1, a_vec,
+                     gm < M, k0 + kc, ke);
+      }
+    } else {
+      for (int e = tid; e < TC_BM * TC_BK; e += TC_THREADS) {
+        const int r = a_kfast ? e / TC_BK : e % TC_BM, k = a_kfast ? e % TC_BK : e / TC_BM;
+        const int gm = m0 + r, gk = k0 + k;
+        const __nv_bfloat16 v = (gm < M && gk < ke) ? A[(int64_t)gm * sam + (int64_t)gk * sak]
+                                                    : __float2bfloat16(0.0f);
+        *reinterpret_cast<__nv_bfloat16 *>(sA + tc_off(r, k)) = v;
+      }
     }
-    for (int e = tid; e < TC_BN * TC_BK; e += TC_THREADS) {
-      const int c = b_kfast ? e / TC_BK : e % TC_BN, k = b_kfast ? e % TC_BK : e / TC_BN;
-      const int gn = n0 + c, gk = k0 + k;
-      const __nv_bfloat16 v = (gn < N && gk < K) ? B[(int64_t)gk * sbk + (int64_t)gn * sbn]
-                                                 : __float2bfloat16(0.0f);
-      *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off(c, k)) = v;
+    if (b_k1) {
+      for (int e = tid; e < TC_BN * (TC_BK / 8); e += TC_THREADS) {
+        const int c = e >> 3, kc = (e & 7) * 8, gn = n0 + c;
+        tc_stage_row(sB + tc_off(c, kc), B + (int64_t)(gn < N ? gn : 0) * sbn, 1, b_vec,
+                     gn < N, k0 + kc, ke);
+      }
+    } else {
+      for (int e = tid; e < TC_BN * TC_BK; e += TC_THREADS) {
+        const int c = b_kfast ? e / TC_BK : e % TC_BN, k = b_kfast ? e % TC_BK : e / TC_BN;
+        const int gn = n0 + c, gk = k0 + k;
+        const __nv_bfloat16 v = (gn < N && gk < ke) ? B[(int64_t)gk * sbk + (int64_t)gn * sbn]
+                                                    : __float2bfloat16(0.0f);
+        *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off(c, k)) = v;
+      }
     }
     // make the generic-proxy writes visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -332,6 +372,28 @@ __global__ void k_to_bf16(int64_t n, const float *x, __nv_bfloat16 *y) {
   if (i < n) y[i] = __float2bfloat16(x[i]);
 }
 
+// y [N][K] = bf16(x [K][N])^T: a weight block with K contiguous, so the
+// forward GEMMs stage their B operand 16 bytes at a time
+__global__ void k_to_bf16_t(int K, int N, const float *x, __nv_bfloat16 *y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)K * N) return;
+  const int k = (int)(i / N), n = (int)(i % N);
+  y[(int64_t)n * K + k] = __float2bfloat16(x[i]);
+}
+
+// C[m][n] (+)= sum over the S partial tiles ws[s][m][n] (split-K GEMMs; a
+// fixed summation order, so results do not depend on scheduling)
+__global__ void k_splitk_reduce(int M, int N, int S, const float *ws, float *C, int64_t ldc,
+                                int accumulate) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)M * N) return;
+  const int m = (int)(i / N), n = (int)(i % N);
+  float v = 0.0f;
+  for (int q = 0; q < S; ++q) v += ws[(int64_t)q * M * N + i];
+  float *dst = C + (int64_t)m * ldc + n;
+  *dst = accumulate ? *dst + v : v;
+}
+
 // column mean and standard deviation of X [M][d] (two-pass, FP64 sums)
 __global__ void k_moments(int64_t M, int d, const float *X, float *mean, float *stdv) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -405,6 +467,9 @@ struct kin_mlp {
   float *p = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
   unsigned char *mask = nullptr;
   __nv_bfloat16 *wb = nullptr;  // bf16 copy of the weight blocks (same offsets)
+  __nv_bfloat16 *wbt = nullptr; // the same blocks transposed ([N][K] at the same offsets)
+  float *ws = nullptr;          // split-K partial tiles
+  int64_t ws_floats = 0;
   int64_t step = 0;
   // activations (capacity rows)
   int64_t cap = 0;
@@ -455,10 +520,28 @@ static void gemm(const kin_mlp *n, cudaStream_t st, int M, int N, int K, bool bf
                  int64_t sam, int64_t sak, const void *B, int64_t sbk, int64_t sbn, float *C,
                  int64_t ldc, int acc) {
   if (bf) {
-    dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
-    k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(M, N, K, (const __nv_bfloat16 *)A, sam, sak,
-                                                 (const __nv_bfloat16 *)B, sbk, sbn, C, ldc, acc,
-                                                 n->err);
+    dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN, 1);
+    // few output tiles and a long K (the weight gradients: K = batch rows):
+    // split K over up to 2 x 152 CTAs, partial tiles reduced in fixed order
+    const int64_t tiles = (int64_t)grid.x * grid.y, kt = (K + TC_BK - 1) / TC_BK;
+    int S = 1;
+    if (tiles < 2 * 152 && kt >= 8) {
+      S = (int)std::min<int64_t>(kt / 4, (2 * 152 + tiles - 1) / tiles);
+      while (S > 1 && (int64_t)S * M * N > n->ws_floats) --S;
+    }
+    if (S > 1) {
+      const int kchunk = (int)((kt + S - 1) / S) * TC_BK;
+      S = (K + kchunk - 1) / kchunk;  // every split holds at least one K slice
+      grid.z = S;
+      k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(M, N, K, (const __nv_bfloat16 *)A, sam, sak,
+                                                   (const __nv_bfloat16 *)B, sbk, sbn, n->ws, N,
+                                                   0, n->err, kchunk, (int64_t)M * N);
+      k_splitk_reduce<<<blocks((int64_t)M * N), 256, 0, st>>>(M, N, S, n->ws, C, ldc, acc);
+    } else {
+      k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(M, N, K, (const __nv_bfloat16 *)A, sam, sak,
+                                                   (const __nv_bfloat16 *)B, sbk, sbn, C, ldc,
+                                                   acc, n->err, (int)kt * TC_BK, 0);
+    }
   } else {
     k_gemm_f32<<<blocks((int64_t)M * N), 256, 0, st>>>(M, N, K, (const float *)A, sam, sak,
                                                        (const float *)B, sbk, sbn, C, ldc, acc);
@@ -471,8 +554,12 @@ static int mlp_forward_packed(kin_mlp *n, int64_t M, cudaStream_t st) {
   for (int l = 0; l < LAYERS; ++l) {
     const void *in = bf ? (l ? (const void *)n->hb[l - 1] : (const void *)n->xb)
                         : (l ? (const void *)n->hf[l - 1] : (const void *)n->xf);
-    const void *W = bf ? (const void *)(n->wb + n->woff[l]) : (const void *)(n->p + n->woff[l]);
-    gemm(n, st, (int)M, n->N[l], n->K[l], bf, in, n->K[l], 1, W, n->N[l], 1, n->C, n->N[l], 0);
+    if (bf)  // B(k, n) = W[k][n] from the transposed copy (K contiguous)
+      gemm(n, st, (int)M, n->N[l], n->K[l], bf, in, n->K[l], 1, n->wbt + n->woff[l], 1,
+           n->K[l], n->C, n->N[l], 0);
+    else
+      gemm(n, st, (int)M, n->N[l], n->K[l], bf, in, n->K[l], 1, n->p + n->woff[l], n->N[l], 1,
+           n->C, n->N[l], 0);
     const int act = l < LAYERS - 1;
     k_bias_act<<<blocks(M * n->N[l]), 256, 0, st>>>(M, n->N[l], n->C, n->p + n->boff[l], n->a[l],
                                                     n->hf[l], bf ? n->hb[l] : nullptr, act);
@@ -514,6 +601,9 @@ static int mlp_pack(kin_mlp *n, const float *X, int64_t M, cudaStream_t st) {
 
 static int mlp_refresh_bf16(kin_mlp *n, cudaStream_t st) {
   k_to_bf16<<<blocks(n->np), 256, 0, st>>>(n->np, n->p, n->wb);
+  for (int l = 0; l < LAYERS; ++l)
+    k_to_bf16_t<<<blocks((int64_t)n->K[l] * n->N[l]), 256, 0, st>>>(
+        n->K[l], n->N[l], n->p + n->woff[l], n->wbt + n->woff[l]);
   KIN_CUDA_TRY(cudaGetLastError());
   return KIN_OK;
 }
@@ -541,6 +631,11 @@ extern "C" int kin_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t 
     off += n->N[l];
   }
   n->np = off;
+  {  // split-K workspace: up to 64 partial tiles of the largest weight block, 64 MB at most
+    int64_t big = 0;
+    for (int l = 0; l < LAYERS; ++l) big = std::max<int64_t>(big, (int64_t)n->K[l] * n->N[l]);
+    n->ws_floats = std::max<int64_t>(big, std::min<int64_t>(64 * big, 16ll << 20));
+  }
   // He-style uniform initialisation, zero biases; padding stays zero
   std::vector<float> p(off, 0.0f);
   std::vector<unsigned char> mask(off, 0);
@@ -562,6 +657,8 @@ extern "C" int kin_mlp_create(int32_t din, int32_t width, int32_t dout, int32_t 
       cudaMalloc(&n->v, sizeof(float) * off) != cudaSuccess ||
       cudaMalloc(&n->mask, off) != cudaSuccess ||
       cudaMalloc(&n->wb, sizeof(__nv_bfloat16) * off) != cudaSuccess ||
+      cudaMalloc(&n->wbt, sizeof(__nv_bfloat16) * off) != cudaSuccess ||
+      cudaMalloc(&n->ws, sizeof(float) * n->ws_floats) != cudaSuccess ||
       cudaMalloc(&n->loss, sizeof(float)) != cudaSuccess ||
       cudaMalloc(&n->err, sizeof(int)) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -593,6 +690,8 @@ extern "C" void kin_mlp_destroy(kin_mlp *n) {
   cudaFree(n->v);
   cudaFree(n->mask);
   cudaFree(n->wb);
+  cudaFree(n->wbt);
+  cudaFree(n->ws);
   cudaFree(n->loss);
   cudaFree(n->err);
   cudaFree(n->xg);

@@ -119,16 +119,34 @@ __host__ __device__ inline size_t warp_e1_bytes(int N, size_t lt) {
   return ((m > v ? m : v) + 7) / 8 * 8;
 }
 
+// Where the complex iteration matrix lives: in the group's shared-memory
+// slice, or after J in the group's global slot, which leaves shared memory
+// to more resident warps while its rows stream through L1/L2.  Measured on
+// 16384 CH4-like states (dt = 1e-4 s): with FP64 matrices the global
+// placement raises the resident warps from 3 to 7 per SM and the rate by
+// 26 %; with FP32 matrices (5 warps per SM in shared memory) it costs 26 %.
+// So FP64 matrices go to the global slot and FP32 ones stay in shared
+// memory (KIN_WARP_E2_GLOBAL_F64 = 0 keeps both in shared memory).
+#ifndef KIN_WARP_E2_GLOBAL_F64
+#define KIN_WARP_E2_GLOBAL_F64 1
+#endif
+__host__ __device__ constexpr bool warp_e2_global(size_t lt) {
+  return KIN_WARP_E2_GLOBAL_F64 && lt == sizeof(double);
+}
+// matrices (N x (N+1), in the matrix type) per group in the global scratch
+__host__ __device__ constexpr int warp_slot_mats(size_t lt) { return warp_e2_global(lt) ? 3 : 1; }
+
 __host__ __device__ inline size_t warp_buf_bytes(int N, int nr, size_t lt) {
   const size_t ld = (size_t)N + 1, nv = (size_t)warp_nv(N);
   size_t b = (5 * nv + (size_t)nr) * sizeof(double);  // C g hs cpk wd, q
   b += warp_e1_bytes(N, lt);                           // E1 (A B Tc mj rW Cj)
-  b += 2 * (size_t)N * ld * lt;                        // E2r E2i
+  if (!warp_e2_global(lt)) b += 2 * (size_t)N * ld * lt;  // E2r E2i
   b += 2 * nv * lt;                                     // v1 v2
   b += 2 * nv * sizeof(int);                            // ip1 ip2
   return (b + 15) / 16 * 16;
 }
 
+// Jglobal: the group's global slot (J, then E2r and E2i when those are global)
 template <typename LT>
 __device__ WarpBuf<LT> carve_warp_buf(char *p, int N, int nr, LT *Jglobal) {
   WarpBuf<LT> w;
@@ -146,7 +164,14 @@ __device__ WarpBuf<LT> carve_warp_buf(char *p, int N, int nr, LT *Jglobal) {
   w.J = Jglobal;
   w.E1 = reinterpret_cast<LT *>(l);
   l += warp_e1_bytes(N, sizeof(LT));
-  w.E2r = reinterpret_cast<LT *>(l);
+  LT *v;
+  if (warp_e2_global(sizeof(LT))) {
+    w.E2r = Jglobal + mat;
+    v = reinterpret_cast<LT *>(l);
+  } else {
+    w.E2r = reinterpret_cast<LT *>(l);
+    v = w.E2r + 2 * mat;
+  }
   w.E2i = w.E2r + mat;
   w.Jd = reinterpret_cast<double *>(w.E2r);
   // the Jacobian assembly's vectors live in the E1 area (sized for both):
@@ -158,7 +183,6 @@ __device__ WarpBuf<LT> carve_warp_buf(char *p, int N, int nr, LT *Jglobal) {
   w.mj = e1 + 3 * nv;
   w.rW = e1 + 4 * nv;
   w.Cj = e1 + 5 * nv;
-  LT *v = w.E2r + 2 * mat;
   w.v1 = v;
   w.v2 = v + nv;
   int *ip = reinterpret_cast<int *>(v + 2 * nv);
