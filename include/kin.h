@@ -332,9 +332,9 @@ int kin_integrate_static(const kin_mech_desc *desc, double *Y, double *T, const 
                          void *stream);
 
 /* The exponential the rate kernels use (Tang's table-driven method, accurate
- * to about 1 ulp for |x| <= 700, the library exp beyond): y[i] = exp(x[i]) for
+ * to about 1 ulp for |x| < 700, the library exp beyond): y[i] = exp(x[i]) for
  * x, y dev [n].  Unit-level entry for testing; needs a mechanism only for
- * its staged 2^(j/128) table. */
+ * its 2^(j/256) table. */
 int kin_exp(kin_mech *m, const double *x, double *y, int64_t n, void *stream);
 
 /* Radau IIA constants the kernels use, computed by the library from closed

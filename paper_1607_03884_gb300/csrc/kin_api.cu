@@ -367,7 +367,7 @@ int kin::build_tables(const kin_mech_desc *d, MechLayout &L, std::vector<double>
       g[4] = a[4] / 20.0; g[5] = a[6] - a[0]; g[6] = -a[5];
     }
   }
-  // 2^(j/128), rounded to double, for the table-driven exponential
+  // 2^(j/256), rounded to double, for the table-driven exponential
   for (int j = 0; j < EXP_TAB; ++j) dt[L.dexp + j] = (double)exp2l((long double)j / EXP_TAB);
   int e = 0, tr = 0;
   for (int i = 0; i < nr; ++i) {

@@ -124,35 +124,34 @@ __device__ __forceinline__ double poly_dcp(const double *c, double T) {
 
 // ---------------------------------------------------------------------------
 // Exponential for the rate expressions: Tang's table-driven method
-// (ACM TOMS 15, 1989).  exp(x) = 2^m 2^(j/128) exp(r) with N = round(128 x /
-// ln 2), j = N mod 128, m = N div 128, r = x - N ln2/128 (|r| <= ln2/256,
-// computed with ln2/128 split into a 29-bit head, so N*head is exact, and a
-// tail); exp(r) = 1 + r + r^2/2 + r^3/6 + r^4/24 + r^5/120 (truncation
-// below 6e-19).  The 128 values 2^(j/128) are rounded doubles computed by the
-// host and staged in shared memory.  Valid for |x| <= 700 (the result stays a
-// normal number); outside that range the library exp() is used.
+// (ACM TOMS 15, 1989).  exp(x) = 2^m 2^(j/256) exp(r) with N = round(256 x /
+// ln 2), j = N mod 256, m = N div 256, r = x - N ln2/256 (|r| <= ln2/512,
+// computed with ln2/256 split into a 29-bit head, so N*head is exact, and a
+// tail); exp(r) = 1 + r + r^2/2 + r^3/6 + r^4/24 (truncation below 4e-17).
+// The 256 values 2^(j/256) are rounded doubles computed by the host.  Valid
+// for |x| < 700 (the result stays a normal number), checked on the high word
+// with integer arithmetic; outside that range the library exp() is used.
 // ---------------------------------------------------------------------------
-constexpr int EXP_TAB = 128;
+constexpr int EXP_TAB = 256;
 
 __device__ __forceinline__ double kexp(double x, const double *tab) {
-  if (!(fabs(x) <= 700.0)) return exp(x);
-  const double inv = 0x1.71547652b82fep+7;    // 128 / ln 2
-  const double hi = 0x1.62e42ff000000p-8;     // ln2/128, 29 significant bits
-  const double lo = -0x1.718432a1b0e26p-42;   // ln2/128 - hi
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x4085E000) return exp(x);  // |x| >= 700, NaN
+  const double inv = 0x1.71547652b82fep+8;    // 256 / ln 2
+  const double hi = 0x1.62e42ff000000p-9;     // ln2/256, 29 significant bits
+  const double lo = -0x1.718432a1b0e26p-43;   // ln2/256 - hi
   const double shifter = 0x1.8p52;            // 1.5 * 2^52: rounds to an integer
   double kd = fma(x, inv, shifter);
   const int N = (int)(unsigned)__double2loint(kd);
   kd -= shifter;
   double r = fma(-kd, hi, x);
   r = fma(-kd, lo, r);
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(q, r, 0.5);
   q = fma(q, r, 1.0);
   const double p = q * r;                     // exp(r) - 1
   const double tj = tab[N & (EXP_TAB - 1)];
   const double v = fma(tj, p, tj);
-  const long long m = (long long)(N >> 7);     // floor division (arithmetic shift)
+  const long long m = (long long)(N >> 8);     // floor division (arithmetic shift)
   return __longlong_as_double(__double_as_longlong(v) + (m << 52));
 }
 
