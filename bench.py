@@ -479,7 +479,10 @@ def cpu_baseline(sample, dt, workload=WORKLOAD, one_core=True):
     el = time.perf_counter() - t0
     out = {"value": sample / el, "unit": "states/s", "cores": O.num_threads(), "kind": "oracle",
            "sample": f"{sample} states drawn (seed 1) from the {workload} workload, dt={dt:g}",
-           "seconds": el, "cpu": cpu_model()}
+           "seconds": el, "cpu": cpu_model(),
+           "build": "gcc " + " ".join(O.CFLAGS) + " (the checker's build: IEEE order, no "
+                    "FMA contraction, no host-specific instructions; OpenMP over states, "
+                    "dynamic schedule of 16)"}
     if one_core:  # the same oracle on one thread, over a quarter of the sample
         m = max(16, sample // 4)
         t0 = time.perf_counter()
