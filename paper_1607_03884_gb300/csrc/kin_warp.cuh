@@ -554,12 +554,17 @@ __device__ __noinline__ int warp_lu_real(int N, int ld, LT *a, int *ip) {
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
       const int i = lane + L * r;
-      if (i > k && i < N) {
-        const LT l = a[i * ld + k] * inv;
-        a[i * ld + k] = l;
-        if (l != LT(0))
-          for (int j = k + 1; j < N; ++j) a[i * ld + j] -= l * a[k * ld + j];
-      }
+      if (i > k && i < N) a[i * ld + k] *= inv;
+    }
+    G::sync();
+    // trailing update with lanes over columns: every lane active while
+    // N - k - 1 >= L, the pivot row's entry held in a register, and columns
+    // whose pivot-row entry is zero skipped (the same arithmetic, entry by
+    // entry, as a row-by-row update that skips zero multipliers)
+    for (int j = k + 1 + lane; j < N; j += L) {
+      const LT u = a[k * ld + j];
+      if (u != LT(0))
+        for (int i = k + 1; i < N; ++i) a[i * ld + j] -= a[i * ld + k] * u;
     }
     G::sync();
   }
@@ -617,13 +622,18 @@ __device__ __noinline__ int warp_lu_cplx(int N, int ld, LT *ar, LT *ai, int *ip)
         cdiv(ar[i * ld + k], ai[i * ld + k], pr, pi, lr, li);
         ar[i * ld + k] = lr;
         ai[i * ld + k] = li;
-        if (lr != LT(0) || li != LT(0))
-          for (int j = k + 1; j < N; ++j) {
-            const LT ur = ar[k * ld + j], ui = ai[k * ld + j];
-            ar[i * ld + j] -= lr * ur - li * ui;
-            ai[i * ld + j] -= lr * ui + li * ur;
-          }
       }
+    }
+    G::sync();
+    // trailing update with lanes over columns (as in warp_lu_real)
+    for (int j = k + 1 + lane; j < N; j += L) {
+      const LT ur = ar[k * ld + j], ui = ai[k * ld + j];
+      if (ur != LT(0) || ui != LT(0))
+        for (int i = k + 1; i < N; ++i) {
+          const LT lr = ar[i * ld + k], li = ai[i * ld + k];
+          ar[i * ld + j] -= lr * ur - li * ui;
+          ai[i * ld + j] -= lr * ui + li * ur;
+        }
     }
     G::sync();
   }

@@ -619,20 +619,23 @@ def split_report(tag, Yg, Tg, Yo, To, T0):
 
 
 def equal_accuracy(tag, mech, sub, dt, Yg, Tg, Yo, To, sel):
-    """The FP32 form's accuracy against the FP64 oracle's, both measured
+    """The GPU result's accuracy against the FP64 oracle's, both measured
     against a tight reference (the oracle at rtol 1e-10, atol 1e-17,
-    untransformed) on the states sel (reading r19; none: nothing to check): the median E_i within
-    twice the oracle's, and at most one more state with E_i > 10.  The
-    method's error control misses a step now and then in either precision
-    (an E_i of 1e3 happens in FP64 too), and FP32 rounding changes which
-    states those are, so the tail is compared by count."""
+    untransformed) on the states sel (readings r19, r20; none: nothing to
+    check): the median E_i within twice the oracle's, and at most one more
+    state with E_i > 10.  The method's error control misses a step now and
+    then in either precision (an E_i of 1e3 happens in FP64 too), and
+    rounding changes which states those are, so the tail is compared by
+    count."""
+    if sel.size == 0:
+        return
     Yx, Tx, cx = O.integrate(mech, sub.subset(sel), dt, rtol=1e-10, atol=1e-17,
                              transform_tol=False)
     assert np.all(cx[:, 7] == 0)
     yx = np.concatenate([Tx[None], Yx[:-1]])
     E32 = O.error_norm(np.concatenate([Tg[None], Yg[:-1]])[:, sel], yx)
     E64 = O.error_norm(np.concatenate([To[None], Yo[:-1]])[:, sel], yx)
-    print(f"{tag}: E against the tight reference on {sel.size} states: FP32 median "
+    print(f"{tag}: E against the tight reference on {sel.size} states: GPU median "
           f"{np.median(E32):.3g} max {E32.max():.3g} (> 10: {int(np.sum(E32 > 10))}); FP64 "
           f"oracle median {np.median(E64):.3g} max {E64.max():.3g} (> 10: {int(np.sum(E64 > 10))})")
     assert np.median(E32) <= 2.0 * np.median(E64) + 1e-3, (np.median(E32), np.median(E64))
@@ -855,6 +858,13 @@ def test_lane_groups_reject_large_mechanisms_and_bad_counts(h2, ch4):
 
 
 def test_warp_layout_fd_jacobian_and_edge_sizes(ch4):
+    """FD Jacobian in the WARP layout, FP64 matrices, 1, 5 and 33 CH4
+    states at dt = 1e-6.  T meets 1e-5 on every state and the median E_i
+    against the FD oracle is below 1.  The two sides' right-hand sides
+    differ by rounding, so their difference quotients differ near the
+    square root of it, and the step sequences may part: past that the
+    states are judged by equal accuracy against a tight reference
+    (reading r20)."""
     mech, mg, st = ch4
     for n in (1, 5, 33):
         sub = st.subset(np.arange(n))
@@ -864,7 +874,23 @@ def test_warp_layout_fd_jacobian_and_edge_sizes(ch4):
         eT, eY, per = parity(Yg, Tg, Yo, To)
         assert eT <= RTOL_PARITY
         E = O.error_norm(np.concatenate([Tg[None], Yg[:-1]]), np.concatenate([To[None], Yo[:-1]]))
-        assert E.max() < 1.0, E.max()
+        assert np.median(E) < 1.0, E
+        equal_accuracy(f"CH4 WARP FD, {n} states", mech, sub, 1e-6, Yg, Tg, Yo, To,
+                       np.where(E > 1.0)[0] if n < 33 else np.arange(n))
+
+
+def test_warp_layout_is_deterministic(ch4):
+    """Lanes of a group share the Newton matrices and vectors in shared
+    memory; a missing barrier would make results depend on timing.  Three
+    runs of 64 CH4 states (FD Jacobian with FP64 matrices; analytic with
+    FP32 matrices) agree bit for bit, counters included."""
+    mech, mg, st = ch4
+    sub = st.subset(np.arange(64))
+    for opt in (dict(jac_fd=True), dict(lu_fp32=True)):
+        runs = [run_gpu(mg, sub, 1e-6, layout="warp", **opt) for _ in range(3)]
+        for r in runs[1:]:
+            for a, b in zip(runs[0], r):
+                np.testing.assert_array_equal(a, b)
 
 
 # ----------------------------------------------------------------------------
