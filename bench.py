@@ -491,18 +491,23 @@ def cpu_baseline(sample, dt, workload=WORKLOAD, one_core=True):
     return out
 
 
+# the sources the thread-per-state kernel is compiled and launched from; the
+# state-per-warp header, the ordering, static-entry and predictor sources
+# generate none of its code
+PLAIN_KERNEL_SOURCES = ("kin_api.cu", "kin_device.cuh", "kin_internal.h", "kin_kernels.cuh",
+                        "kin_radau.cuh", "kin_tu_16f.cu")
+
+
 def kernel_digest():
-    """Digest of the sources that define and launch the integration kernels
-    (every CUDA source but the predictor's): a traffic figure taken from
-    other sources is void."""
+    """Digest of the sources that define and launch the thread-per-state
+    integration kernel, whose DRAM traffic profiles/dram_traffic.json
+    records: a traffic figure taken from other sources is void."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1607_03884_gb300", "csrc")
-    files = [os.path.join(d, f) for f in sorted(os.listdir(d))
-             if f.endswith((".cu", ".cuh", ".h")) and f != "kin_mlp.cu"]
-    for path in files:
-        h.update(os.path.basename(path).encode())
-        with open(path, "rb") as fh:
+    for name in PLAIN_KERNEL_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
