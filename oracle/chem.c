@@ -369,3 +369,169 @@ int orc_jac_fd(const orc_mech *m, double P, const double *y, const double *f0, d
   fd_ctx c = {m, P};
   return orc_fd_jacobian(m->ns, fd_rhs, &c, 0.0, y, f0, h, scal, J);
 }
+
+/* ------------------------------------------------------------------------
+ * Concentration-based form: the reformulation the paper proposes for a
+ * sparse Jacobian and a sparse LU (Sec. 3.3 and Sec. 4, after Schwer et al.
+ * and the planned sparse pyJac).  The state is extensive, per unit mass of
+ * mixture: phi = [T, V, n_0 .. n_{ns-2}] with V the volume (m^3) and n_k the
+ * moles (kmol) of every species but the last, the inert bath gas, whose
+ * moles close the ideal-gas law at the fixed pressure:
+ *   C_k = n_k / V (k < in),   Ctot = P / (Ru T),   C_in = Ctot - sum_{k<in} C_k
+ *   dn_k/dt = V wdot_k                                  (k < in)
+ *   dT/dt   = -sum_k H_k wdot_k / sum_k C_k Cp_k        (the same energy equation)
+ *   dV/dt   = V (sum_k wdot_k / Ctot + (dT/dt) / T)     (d/dt of P V = n Ru T)
+ * with H_k = Ru T (h/RT)_k and Cp_k = Ru (cp/R)_k.  The Jacobian goes through
+ * the concentrations as orc_jac does: dq/dC (nr x ns) times dC/dphi
+ * (ns x (ns+1)), plus the explicit temperature dependences.  A species pair
+ * is coupled only through a reaction that both take part in, or a collision
+ * efficiency that differs from the bath gas's; rows and columns of T and V
+ * are full.
+ * ---------------------------------------------------------------------- */
+
+/* C[ns] of the state phi; returns Ctot */
+static double conc_of(const orc_mech *m, double P, const double *phi, double *C) {
+  int in = m->ns - 1;
+  double T = phi[0], V = phi[1], Ctot = P / (ORC_RU * T), s = 0.0;
+  for (int k = 0; k < in; ++k) {
+    C[k] = phi[2 + k] / V;
+    s += C[k];
+  }
+  C[in] = Ctot - s;
+  return Ctot;
+}
+
+/* molar production rates from (T, C) */
+static void wdot_of_C(const orc_mech *m, double T, const double *C, const double *h_RT,
+                      const double *s_R, double *wdot) {
+  for (int k = 0; k < m->ns; ++k) wdot[k] = 0.0;
+  for (int i = 0; i < m->nr; ++i) {
+    rxn_terms r = reaction(m, i, T, C, h_RT, s_R);
+    double q = r.phi * (r.kf * r.fwd - r.kr * r.rev);
+    for (int k = 0; k < m->ns; ++k) wdot[k] += nu_of(m, i, k) * q;
+  }
+}
+
+int orc_rhs_conc(const orc_mech *m, double P, const double *phi, double *f) {
+  int ns = m->ns, in = ns - 1;
+  double T = phi[0], V = phi[1];
+  double *C = malloc(sizeof(double) * 5 * ns), *wdot = C + ns, *cp = wdot + ns, *h = cp + ns,
+         *s = h + ns;
+  double Ctot = conc_of(m, P, phi, C);
+  orc_thermo(m, T, cp, h, s);
+  wdot_of_C(m, T, C, h, s, wdot);
+  double Hs = 0.0, Cs = 0.0, Ws = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    Hs += h[k] * wdot[k];
+    Cs += C[k] * cp[k];
+    Ws += wdot[k];
+  }
+  double fT = -T * Hs / Cs;
+  f[0] = fT;
+  f[1] = V * (Ws / Ctot + fT / T);
+  for (int k = 0; k < in; ++k) f[2 + k] = V * wdot[k];
+  int ok = 1;
+  for (int k = 0; k < ns + 1; ++k) ok &= isfinite(f[k]);
+  free(C);
+  return ok ? 0 : ORC_NONFINITE;
+}
+
+/* J[i*(ns+1) + j] = d f_i / d phi_j of the concentration-based form */
+int orc_jac_conc(const orc_mech *m, double P, const double *phi, double *J) {
+  int ns = m->ns, nr = m->nr, in = ns - 1, N = ns + 1;
+  double T = phi[0], V = phi[1];
+  double *C = calloc((size_t)ns * 6, sizeof(double));
+  double *cp = C + ns, *h = cp + ns, *s = h + ns, *dcp = s + ns, *wdot = dcp + ns;
+  double *dqdC = calloc((size_t)nr * ns, sizeof(double));
+  double *dqdT = calloc((size_t)nr, sizeof(double));
+  double *dCdp = calloc((size_t)ns * N, sizeof(double));   /* d C_k / d phi_j */
+  double *dqdp = calloc((size_t)nr * N, sizeof(double));
+  double *dwdp = calloc((size_t)ns * N, sizeof(double));
+  double Ctot = conc_of(m, P, phi, C);
+  orc_thermo(m, T, cp, h, s);
+  thermo_dcp(m, T, dcp);
+  for (int k = 0; k < ns; ++k) wdot[k] = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    rxn_terms r = reaction(m, i, T, C, h, s);
+    const int32_t *re = m->reac + 3 * i, *pr = m->prod + 3 * i;
+    double Rnet = r.kf * r.fwd - r.kr * r.rev;
+    double q = r.phi * Rnet;
+    for (int k = 0; k < ns; ++k) wdot[k] += nu_of(m, i, k) * q;
+    for (int k = 0; k < ns; ++k) {
+      double d = r.phi * (r.kf * mass_action_dC(re, C, k) - r.kr * mass_action_dC(pr, C, k));
+      if (m->rtype[i] != 0) d += Rnet * r.dphi_dM * m->eff[(size_t)i * ns + k];
+      dqdC[(size_t)i * ns + k] = d;
+    }
+    dqdT[i] = r.phi * (r.kf * r.dlnkf_dT * r.fwd - r.kr * r.dlnkr_dT * r.rev) + Rnet * r.dphi_dT;
+  }
+  /* dC/dphi: column 0 is T, column 1 is V, column 2+l is n_l */
+  double Sact = 0.0;
+  for (int k = 0; k < in; ++k) Sact += C[k];
+  for (int k = 0; k < in; ++k) {
+    dCdp[(size_t)k * N + 1] = -C[k] / V;
+    dCdp[(size_t)k * N + 2 + k] = 1.0 / V;
+  }
+  dCdp[(size_t)in * N + 0] = -Ctot / T;
+  dCdp[(size_t)in * N + 1] = Sact / V;
+  for (int l = 0; l < in; ++l) dCdp[(size_t)in * N + 2 + l] = -1.0 / V;
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < N; ++j) {
+      double d = (j == 0) ? dqdT[i] : 0.0;
+      for (int k = 0; k < ns; ++k) d += dqdC[(size_t)i * ns + k] * dCdp[(size_t)k * N + j];
+      dqdp[(size_t)i * N + j] = d;
+    }
+  for (int k = 0; k < ns; ++k)
+    for (int j = 0; j < N; ++j) {
+      double d = 0.0;
+      for (int i = 0; i < nr; ++i) d += nu_of(m, i, k) * dqdp[(size_t)i * N + j];
+      dwdp[(size_t)k * N + j] = d;
+    }
+  /* mixture sums and their derivatives */
+  double Hs = 0.0, Cs = 0.0, Ws = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    Hs += h[k] * wdot[k];
+    Cs += C[k] * cp[k];
+    Ws += wdot[k];
+  }
+  double fT = -T * Hs / Cs;
+  for (int j = 0; j < N; ++j) {
+    double a = 0.0, c = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      a += T * h[k] * dwdp[(size_t)k * N + j];
+      c += cp[k] * dCdp[(size_t)k * N + j];
+    }
+    if (j == 0)
+      for (int k = 0; k < ns; ++k) {
+        a += cp[k] * wdot[k];   /* d(T h_k)/dT = cp_k (h in units of RT) */
+        c += C[k] * dcp[k];
+      }
+    /* T row: f_T = -(T Hs) / Cs; a = d(T Hs)/dphi_j, c = dCs/dphi_j */
+    J[(size_t)0 * N + j] = -a / Cs + (T * Hs) * c / (Cs * Cs);
+  }
+  for (int j = 0; j < N; ++j) {
+    double dW = 0.0;
+    for (int k = 0; k < ns; ++k) dW += dwdp[(size_t)k * N + j];
+    double JT = J[(size_t)0 * N + j];
+    /* V row: f_V = V (Ws / Ctot + fT / T), Ctot = P / (Ru T) */
+    double inner = dW / Ctot + JT / T;
+    if (j == 0) inner += Ws / (Ctot * T) - fT / (T * T);
+    double dV = V * inner;
+    if (j == 1) dV += Ws / Ctot + fT / T;
+    J[(size_t)1 * N + j] = dV;
+    /* species rows: f_k = V wdot_k */
+    for (int k = 0; k < in; ++k) {
+      double d = V * dwdp[(size_t)k * N + j];
+      if (j == 1) d += wdot[k];
+      J[(size_t)(2 + k) * N + j] = d;
+    }
+  }
+  int ok = 1;
+  for (size_t q = 0; q < (size_t)N * N; ++q) ok &= isfinite(J[q]);
+  free(C);
+  free(dqdC);
+  free(dqdT);
+  free(dCdp);
+  free(dqdp);
+  free(dwdp);
+  return ok ? 0 : ORC_NONFINITE;
+}

@@ -17,8 +17,13 @@
  *     atol/rtol as in Sec. 2.1;
  *   - per-state statistics (internal step counts d_i, Sec. 3.3).
  *
+ *   - the concentration-based (extensive, moles) form of the same reactor,
+ *     whose Jacobian is sparse (Sec. 3.3, Sec. 4): chem.c, orc_rhs_conc.
+ *
  * State vector: y = [T, Y_0 .. Y_{ns-2}], N = ns; the last species is inert
- * and its mass fraction is 1 - sum of the others.  Units: SI with kmol.
+ * and its mass fraction is 1 - sum of the others.  Units: SI with kmol.  The
+ * concentration-based form's state is phi = [T, V, n_0 .. n_{ns-2}] per unit
+ * mass (N = ns + 1).
  */
 #ifndef KIN_ORACLE_H
 #define KIN_ORACLE_H
@@ -56,6 +61,7 @@ typedef struct {
   int jac_kind;        /* 0 analytical, 1 finite difference */
   const double *z0;    /* optional first-step stage guess [3*N] or NULL */
   double *z_first_out; /* optional [3*N]: stage increments of the first accepted step */
+  int form;            /* batch driver: 0 mass fractions, 1 concentration-based (moles) */
 } orc_opts;
 
 typedef struct {
@@ -86,6 +92,8 @@ int orc_jac_fd(const orc_mech *m, double P, const double *y, const double *f0,
 void orc_rate_constants(const orc_mech *m, double T, const double *C,
                         double *kf_eff, double *kr_eff);
 void orc_wdot(const orc_mech *m, double T, double P, const double *Yfull, double *wdot);
+int orc_rhs_conc(const orc_mech *m, double P, const double *phi, double *f);
+int orc_jac_conc(const orc_mech *m, double P, const double *phi, double *J);
 
 /* linalg.c */
 int orc_lu_real(int n, double *a, int32_t *ipiv);

@@ -29,6 +29,7 @@ SOURCES = ["chem.c", "linalg.c", "radau.c", "batch.c"]
 # timed CPU baseline is this same build.
 CFLAGS = ["-O3", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math", "-ffp-contract=off"]
 LIB_NAME = "liboracle.so"
+RU = 8314.46261815324  # J/(kmol K), as oracle.h
 _lock = threading.Lock()
 _lib = None
 
@@ -57,7 +58,7 @@ class _Opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("transform_tol", C.c_int),
                 ("nit", C.c_int), ("h0", C.c_double), ("hfixed", C.c_double),
                 ("max_steps", C.c_int), ("jac_kind", C.c_int), ("z0", C.c_void_p),
-                ("z_first_out", C.c_void_p)]
+                ("z_first_out", C.c_void_p), ("form", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -94,6 +95,8 @@ def lib():
             L.orc_jac_fd.argtypes = [vp, d, vp, vp, d, vp, vp]
             L.orc_rate_constants.argtypes = [vp, d, vp, vp, vp]
             L.orc_wdot.argtypes = [vp, d, d, vp, vp]
+            L.orc_rhs_conc.argtypes = [vp, d, vp, vp]
+            L.orc_jac_conc.argtypes = [vp, d, vp, vp]
             L.orc_lu_real.argtypes = [i, vp, vp]
             L.orc_lu_solve_real.argtypes = [i, vp, vp, vp]
             L.orc_lu_cplx.argtypes = [i, vp, vp]
@@ -169,6 +172,51 @@ def jac_fd(mech, P, y, f0, h, scal):
     return J, rc
 
 
+FORMS = {"massfrac": 0, "conc": 1}
+
+
+def rhs_conc(mech, P, phi):
+    """f(phi) of the concentration-based form, phi = [T, V, n_0..n_{ns-2}]
+    per unit mass (chem.c orc_rhs_conc; Sec. 3.3, Sec. 4)."""
+    om = _as_om(mech)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    f = np.zeros(om.ns + 1)
+    rc = lib().orc_rhs_conc(om.ptr, float(P), _p(phi), _p(f))
+    return f, rc
+
+
+def jac_conc(mech, P, phi):
+    om = _as_om(mech)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    J = np.zeros((om.ns + 1, om.ns + 1))
+    rc = lib().orc_jac_conc(om.ptr, float(P), _p(phi), _p(J))
+    return J, rc
+
+
+def to_conc(mech, Y, T, P):
+    """phi = [T, V, n_0..n_{ns-2}] per unit mass of the states (Y [ns, n] or
+    [ns], T, P): n_k = Y_k / W_k, V = Ru T sum_k (Y_k / W_k) / P."""
+    W = np.asarray(mech.W, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    nk = Y / (W[:, None] if Y.ndim == 2 else W)
+    V = RU * np.asarray(T, dtype=np.float64) * nk.sum(axis=0) / np.asarray(P, dtype=np.float64)
+    return np.concatenate([np.atleast_1d(T)[None] if Y.ndim == 2 else [T],
+                           np.atleast_1d(V)[None] if Y.ndim == 2 else [V], nk[:-1]])
+
+
+def from_conc(mech, phi, P):
+    """(Y [ns, ...], T) of phi: the bath gas's moles close P V = n Ru T and
+    Y_k = W_k n_k over the mixture's mass."""
+    W = np.asarray(mech.W, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    T, V, n = phi[0], phi[1], phi[2:]
+    nin = np.asarray(P, dtype=np.float64) * V / (RU * T) - n.sum(axis=0)
+    nall = np.concatenate([n, np.asarray(nin)[None]])
+    w = W[:, None] if phi.ndim == 2 else W
+    mass = (w * nall).sum(axis=0)
+    return w * nall / mass, T
+
+
 def rate_constants(mech, T, Cc):
     om = _as_om(mech)
     Cc = np.ascontiguousarray(Cc, dtype=np.float64)
@@ -223,10 +271,10 @@ def tableau():
 
 
 def make_opts(rtol=1e-6, atol=1e-10, transform_tol=True, nit=7, h0=0.0, hfixed=0.0,
-              max_steps=100000, jac_kind=0, z0=None, z_first_out=None):
+              max_steps=100000, jac_kind=0, z0=None, z_first_out=None, form=0):
     o = _Opts(rtol, atol, int(transform_tol), nit, h0, hfixed, max_steps, jac_kind,
               None if z0 is None else _p(z0).value,
-              None if z_first_out is None else _p(z_first_out).value)
+              None if z_first_out is None else _p(z_first_out).value, int(form))
     return o
 
 
@@ -322,8 +370,11 @@ def radau(f, jacobian, y0, t0, t1, **kw):
 
 
 def integrate(mech, states, dt, *, rtol=1e-6, atol=1e-10, jac_kind=0, nthreads=0,
-              max_steps=100000, h0=0.0, hfixed=0.0, transform_tol=True, nit=7):
-    """Integrate a batch of states over dt.  Returns (Y, T, counters[n, 8])."""
+              max_steps=100000, h0=0.0, hfixed=0.0, transform_tol=True, nit=7,
+              form="massfrac"):
+    """Integrate a batch of states over dt.  Returns (Y, T, counters[n, 8]).
+    form "conc" integrates the concentration-based form (the tolerances then
+    weigh phi = [T, V, n_0..n_{ns-2}])."""
     om = _as_om(mech)
     Y = np.array(states.Y, dtype=np.float64, order="C")
     T = np.array(states.T, dtype=np.float64)
@@ -331,7 +382,7 @@ def integrate(mech, states, dt, *, rtol=1e-6, atol=1e-10, jac_kind=0, nthreads=0
     n = T.shape[0]
     cnt = np.zeros((n, 8), dtype=np.int32)
     o = make_opts(rtol=rtol, atol=atol, jac_kind=jac_kind, max_steps=max_steps, h0=h0,
-                  hfixed=hfixed, transform_tol=transform_tol, nit=nit)
+                  hfixed=hfixed, transform_tol=transform_tol, nit=nit, form=FORMS[form])
     lib().orc_integrate_batch(om.ptr, n, _p(Y), _p(T), _p(P), float(dt), C.byref(o), None,
                               _p(cnt), int(nthreads))
     return Y, T, cnt
