@@ -346,6 +346,69 @@ int kin_exp(kin_mech *m, const double *x, double *y, int64_t n, void *stream);
 int kin_radau_constants(double *out, int32_t len);
 
 /* ---------------------------------------------------------------------------
+ * Concentration-based form with a sparse LU (Sec. 3.3 and Sec. 4: the paper
+ * proposes reformulating the kinetics in species concentrations so that the
+ * Jacobian is sparse and the Newton matrices admit a sparse factorisation).
+ * Each state is integrated in phi = [T, V, n_0 .. n_{ns-2}] per unit mass of
+ * mixture at constant pressure: the volume and the moles of every species
+ * but the last (the inert bath gas, whose moles close P V = n Ru T):
+ *   dn_k/dt = V wdot_k,  dT/dt = -sum_k H_k wdot_k / sum_k C_k Cp_k,
+ *   dV/dt = V (Ru T / P sum_k wdot_k + (dT/dt) / T),  C_k = n_k / V.
+ * The Jacobian couples two species only through a reaction both take part
+ * in, or a collision efficiency that differs from the bath gas's; the T and
+ * V rows and columns are full.  Radau IIA is the same method as
+ * kin_integrate's, with rtol/atol weighing phi; inputs and outputs are mass
+ * fractions (n_k = Y_k / W_k, V = 1 / rho on entry; Y_k = W_k n_k over the
+ * mixture's mass on exit), so the results are those of the same reactor
+ * integrated to the same tolerances in other variables.
+ * ------------------------------------------------------------------------- */
+typedef struct kin_conc kin_conc;
+
+/* Symbolic analysis only (host; no GPU): the elimination order and the
+ * filled pattern kin_conc_create would use.  The species are ordered by
+ * minimum degree of the symmetric species structure (ties to the lower
+ * index), T and V last; the LU takes its pivots in that order, without
+ * pivoting.  var host [ns+1] or NULL: var[g] = the phi index (0 T, 1 V,
+ * 2 + k species k) at elimination position g.  pattern host [(ns+1)^2] or
+ * NULL: 1 where L + U (diagonal included) may be non-zero, row-major in
+ * elimination order.  counts host [4] or NULL: non-zeros of J's pattern,
+ * non-zeros of L + U, operations of one real factorisation over the pattern
+ * (a division and the multiplier products per pivot, 2 per update) and of
+ * one real solve (2 per off-diagonal entry and N divisions).  Errors:
+ * KIN_ERR_INVALID_ARG (NULL desc or arrays, ns outside [2, KIN_MAX_SPECIES],
+ * nr < 1), KIN_ERR_MECH (a slot out of range, the last species reacting),
+ * KIN_ERR_UNSUPPORTED (the last species has a non-default collision
+ * efficiency, which would couple every species). */
+int kin_conc_analyse(const kin_mech_desc *desc, int32_t *var, uint8_t *pattern,
+                     int64_t *counts);
+
+/* Build the device tables and the sparse structure of a mechanism for the
+ * concentration-based form on the current device; *out receives a handle to
+ * free with kin_conc_destroy.  Errors: those of kin_mech_create and
+ * kin_conc_analyse, and KIN_ERR_UNSUPPORTED for ns > 63. */
+int kin_conc_create(const kin_mech_desc *desc, kin_conc **out);
+
+/* Free a plan and its workspace (NULL is ignored; no work may be in flight). */
+void kin_conc_destroy(kin_conc *c);
+
+/* kin_integrate_ex in the concentration-based form: Y dev [ns][n] in/out,
+ * T dev [n] in/out, P dev [n].  One state per warp (32 lanes), Newton
+ * matrices dense in shared memory or a global slot as in KIN_LAYOUT_WARP but
+ * factorised and solved over the sparse pattern.  Options (NULL = defaults):
+ * layout WARP or AUTO, lanes 0 or 32, analytical Jacobian, no h_fixed, no z0
+ * or z_first (KIN_ERR_UNSUPPORTED otherwise); lu_fp32, max_steps, nit,
+ * transform_tol, stop_after, h0, h_first and order as kin_integrate_ex.  A
+ * zero pivot counts as a singular matrix (KIN_STATE_SINGULAR after 5 in a
+ * row).  status and counters as kin_integrate_ex.  Asynchronous on stream;
+ * calls on one kin_conc must not overlap. */
+int kin_integrate_conc(kin_conc *c, double *Y, double *T, const double *P, int64_t n, double dt,
+                       double rtol, double atol, const kin_options *opt, int32_t *status,
+                       int32_t *counters, void *stream);
+
+/* Totals of the last kin_integrate_conc call, as kin_get_stats. */
+int kin_conc_get_stats(kin_conc *c, int64_t *out);
+
+/* ---------------------------------------------------------------------------
  * Step/guess predictor (the learned part; the paper has no counterpart).
  * An MLP x (din) -> 3 x [Linear(width) -> SiLU] -> Linear(dout) trained on
  * first steps the integrator itself produced, predicting the first internal

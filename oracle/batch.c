@@ -12,7 +12,7 @@
  *
  * With o->form = 1 each state is integrated in the concentration-based form
  * (chem.c): per unit mass, n_k = Y_k / W_k and V = Ru T sum_k (Y_k / W_k) / P
- * on entry; on exit the bath gas's moles close the ideal-gas law and the
+ * on entry, with the moles' absolute tolerance atol / W_k (T's and V's atol); on exit the bath gas's moles close the ideal-gas law and the
  * mass fractions are W_k n_k over the mixture's mass sum_k W_k n_k.
  */
 #include <stdlib.h>
@@ -53,8 +53,16 @@ static void integrate_conc(const orc_mech *m, double *Yi, int64_t n, double *Ti,
   phi[0] = *Ti;
   phi[1] = ORC_RU * *Ti * S / P;
   for (int k = 0; k < in; ++k) phi[2 + k] = Yi[(size_t)k * n] / m->W[k];
+  /* the moles' absolute tolerance is atol / W_k, so a mole error weighs as
+   * the mass-fraction error W_k dn_k does in the mass-fraction form */
+  double *aw = malloc(sizeof(double) * (ns + 1));
+  aw[0] = aw[1] = 1.0;
+  for (int k = 0; k < in; ++k) aw[2 + k] = 1.0 / m->W[k];
+  orc_opts oc = *o;
+  oc.atol_scale = aw;
   kin_ctx ctx = {m, P, o->jac_kind};
-  orc_radau(ns + 1, conc_rhs, conc_jac, &ctx, 0.0, dt, phi, o, st);
+  orc_radau(ns + 1, conc_rhs, conc_jac, &ctx, 0.0, dt, phi, &oc, st);
+  free(aw);
   double T = phi[0], V = phi[1], nin = P * V / (ORC_RU * T), mass = 0.0;
   for (int k = 0; k < in; ++k) {
     nin -= phi[2 + k];

@@ -62,6 +62,8 @@ typedef struct {
   const double *z0;    /* optional first-step stage guess [3*N] or NULL */
   double *z_first_out; /* optional [3*N]: stage increments of the first accepted step */
   int form;            /* batch driver: 0 mass fractions, 1 concentration-based (moles) */
+  const double *atol_scale; /* optional [N]: component i's absolute tolerance is
+                               atol * atol_scale[i] (NULL: atol for all) */
 } orc_opts;
 
 typedef struct {

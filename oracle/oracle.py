@@ -58,7 +58,7 @@ class _Opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("transform_tol", C.c_int),
                 ("nit", C.c_int), ("h0", C.c_double), ("hfixed", C.c_double),
                 ("max_steps", C.c_int), ("jac_kind", C.c_int), ("z0", C.c_void_p),
-                ("z_first_out", C.c_void_p), ("form", C.c_int)]
+                ("z_first_out", C.c_void_p), ("form", C.c_int), ("atol_scale", C.c_void_p)]
 
 
 class _Stats(C.Structure):
@@ -271,10 +271,12 @@ def tableau():
 
 
 def make_opts(rtol=1e-6, atol=1e-10, transform_tol=True, nit=7, h0=0.0, hfixed=0.0,
-              max_steps=100000, jac_kind=0, z0=None, z_first_out=None, form=0):
+              max_steps=100000, jac_kind=0, z0=None, z_first_out=None, form=0,
+              atol_scale=None):
     o = _Opts(rtol, atol, int(transform_tol), nit, h0, hfixed, max_steps, jac_kind,
               None if z0 is None else _p(z0).value,
-              None if z_first_out is None else _p(z_first_out).value, int(form))
+              None if z_first_out is None else _p(z_first_out).value, int(form),
+              None if atol_scale is None else _p(atol_scale).value)
     return o
 
 
@@ -373,8 +375,8 @@ def integrate(mech, states, dt, *, rtol=1e-6, atol=1e-10, jac_kind=0, nthreads=0
               max_steps=100000, h0=0.0, hfixed=0.0, transform_tol=True, nit=7,
               form="massfrac"):
     """Integrate a batch of states over dt.  Returns (Y, T, counters[n, 8]).
-    form "conc" integrates the concentration-based form (the tolerances then
-    weigh phi = [T, V, n_0..n_{ns-2}])."""
+    form "conc" integrates the concentration-based form: the tolerances weigh
+    phi = [T, V, n_0..n_{ns-2}], the moles with absolute tolerance atol / W_k."""
     om = _as_om(mech)
     Y = np.array(states.Y, dtype=np.float64, order="C")
     T = np.array(states.T, dtype=np.float64)

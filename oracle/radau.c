@@ -28,8 +28,8 @@
  * atol' = rtol' atol/rtol; nit = 7; kappa Tol = max(10 u/rtol', min(0.03,
  * sqrt(rtol'))), u = 1e-16; the first step from the starting-step heuristic
  * of Hairer-Norsett-Wanner Vol. I Sec. II.4 with error order 4; error weights
- * scal = atol' + rtol' |y_n|; a non-finite stage value counts as a Newton
- * failure (h halved).
+ * scal = atol' aw_i + rtol' |y_n| (aw_i = o->atol_scale[i], else 1); a
+ * non-finite stage value counts as a Newton failure (h halved).
  */
 #include <float.h>
 #include <math.h>
@@ -156,11 +156,13 @@ static double wrms(int n, const double *v, const double *scal) {
   return sqrt(s / n);
 }
 
-/* Starting step (Hairer, Norsett & Wanner Vol. I, Sec. II.4), error order 4. */
-double orc_initial_step(int n, orc_rhs_fn f, void *ctx, double t0, double t1, const double *y,
-                        const double *f0, double rtol, double atol, int *nfcn) {
+/* Starting step (Hairer, Norsett & Wanner Vol. I, Sec. II.4), error order 4,
+ * with the weights atol aw_i + rtol |y_i| (aw NULL: 1). */
+static double initial_step_w(int n, orc_rhs_fn f, void *ctx, double t0, double t1,
+                             const double *y, const double *f0, double rtol, double atol,
+                             const double *aw, int *nfcn) {
   double *sc = malloc(sizeof(double) * 3 * n), *y1 = sc + n, *f1 = y1 + n;
-  for (int i = 0; i < n; ++i) sc[i] = atol + rtol * fabs(y[i]);
+  for (int i = 0; i < n; ++i) sc[i] = atol * (aw ? aw[i] : 1.0) + rtol * fabs(y[i]);
   double d0 = wrms(n, y, sc), d1 = wrms(n, f0, sc);
   double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
   h0 = fmin(h0, t1 - t0);
@@ -179,6 +181,11 @@ double orc_initial_step(int n, orc_rhs_fn f, void *ctx, double t0, double t1, co
   }
   free(sc);
   return fmin(h, t1 - t0);
+}
+
+double orc_initial_step(int n, orc_rhs_fn f, void *ctx, double t0, double t1, const double *y,
+                        const double *f0, double rtol, double atol, int *nfcn) {
+  return initial_step_w(n, f, ctx, t0, t1, y, f0, rtol, atol, NULL, nfcn);
 }
 
 /* One-sided difference-quotient Jacobian "based on that of CVODE" (Sec. 2.1,
@@ -221,6 +228,7 @@ int orc_radau(int n, orc_rhs_fn f, orc_jac_fn jac, void *ctx, double t0, double 
   const double *Tm = tb.T, *TI = tb.TI;
   const double d1 = tb.e[0] / tb.gamma0, d2 = tb.e[1] / tb.gamma0, d3 = tb.e[2] / tb.gamma0;
   double rtol = o->rtol, atol = o->atol;
+  const double *aw = o->atol_scale; /* per-component factor on atol, NULL = 1 */
   if (o->transform_tol) {
     double quot = atol / rtol;
     rtol = 0.1 * pow(rtol, 2.0 / 3.0);
@@ -251,10 +259,11 @@ int orc_radau(int n, orc_rhs_fn f, orc_jac_fn jac, void *ctx, double t0, double 
     goto done;
   }
   st->nfcn = 1;
-  for (int i = 0; i < n; ++i) scal[i] = atol + rtol * fabs(y[i]);
+  for (int i = 0; i < n; ++i) scal[i] = atol * (aw ? aw[i] : 1.0) + rtol * fabs(y[i]);
   int nfcn_h = 0;
   double h = fixed ? o->hfixed
-                   : (o->h0 > 0.0 ? o->h0 : orc_initial_step(n, f, ctx, t0, t1, y, f0, rtol, atol, &nfcn_h));
+                   : (o->h0 > 0.0 ? o->h0
+                                  : initial_step_w(n, f, ctx, t0, t1, y, f0, rtol, atol, aw, &nfcn_h));
   st->nfcn += nfcn_h;
   h = fmin(h, hmax);
   int last = 0;
@@ -500,7 +509,7 @@ int orc_radau(int n, orc_rhs_fn f, orc_jac_fn jac, void *ctx, double t0, double 
         a2[i] = (ak - a1[i]) / (c1 - 1.0);
         a3[i] = a2[i] - acont3;
       }
-      for (int i = 0; i < n; ++i) scal[i] = atol + rtol * fabs(y[i]);
+      for (int i = 0; i < n; ++i) scal[i] = atol * (aw ? aw[i] : 1.0) + rtol * fabs(y[i]);
       caljac = 0;
       if (last) {
         st->h_last = hopt;

@@ -807,6 +807,34 @@ __device__ int warp_factor(int N, const WarpBuf<LT> &b, double h) {
   return warp_lu_cplx<L, LT>(N, ld, b.E2r, b.E2i, b.ip2);
 }
 
+// The system a group integrates, as a policy of the step drivers below: its
+// size n(), the absolute tolerance's factor per element atol_w(), right-hand
+// side (and Jacobian) chem(), factorisation of E1 and E2 factor(), and the
+// two solves.  MassFracSys is the mass-fraction reactor
+// with dense Newton matrices and partial pivoting; kin_conc.cuh adds the
+// concentration-based form with a sparse LU.
+template <int L, typename LT>
+struct MassFracSys {
+  using WV = WVecT<Grp<L>::WR>;
+  const MechView *m;
+  __device__ __forceinline__ int n() const { return m->ns; }
+  // factor on atol of element g's error weight atol a_g + rtol |y_g|
+  __device__ __forceinline__ double atol_w(int) const { return 1.0; }
+  __device__ __forceinline__ int chem(const WarpBuf<LT> &b, double P, const WV &y, WV &f,
+                                      bool wantJ) const {
+    return warp_chem<L, LT>(*m, b, P, y, f, wantJ);
+  }
+  __device__ __forceinline__ int factor(const WarpBuf<LT> &b, double h) const {
+    return warp_factor<L, LT>(m->ns, b, h);
+  }
+  __device__ __forceinline__ void solve_real(const WarpBuf<LT> &b, WV &x) const {
+    warp_solve_real<L, LT>(m->ns, b.ld, b.E1, b.ip1, b.v1, x);
+  }
+  __device__ __forceinline__ void solve_cplx(const WarpBuf<LT> &b, WV &xr, WV &xi) const {
+    warp_solve_cplx<L, LT>(m->ns, b.ld, b.E2r, b.E2i, b.ip2, b.v1, b.v2, xr, xi);
+  }
+};
+
 template <int L>
 __device__ void warp_start_values(int N, WStateT<Grp<L>::WR> &w, const StepState &s,
                                   const RadauParams &p, int64_t idx) {
@@ -858,16 +886,18 @@ __device__ __forceinline__ double wrms_wi(int N, const WVecT<Grp<L>::WR> &v,
 
 // E1 solve for the error estimate, with one FP64-residual refinement when
 // the factorisation is FP32 (as solve_e1_refined).
-template <int L, typename LT>
-__device__ void warp_solve_e1(int N, const WarpBuf<LT> &b, double h, WVecT<Grp<L>::WR> &x) {
+template <int L, typename LT, class Sys>
+__device__ void warp_solve_e1(const Sys &sys, const WarpBuf<LT> &b, double h,
+                              WVecT<Grp<L>::WR> &x) {
   constexpr int WR = Grp<L>::WR;
+  const int N = sys.n();
   if (sizeof(LT) == sizeof(double)) {
-    warp_solve_real<L, LT>(N, b.ld, b.E1, b.ip1, b.v1, x);
+    sys.solve_real(b, x);
     return;
   }
   const int lane = Grp<L>::lane();
   const WVecT<WR> rhs = x;
-  warp_solve_real<L, LT>(N, b.ld, b.E1, b.ip1, b.v1, x);
+  sys.solve_real(b, x);
   // residual r = rhs - (gamma/h x - J x)
   const double fac1 = RC.gam / h;
   WVecT<WR> res;
@@ -884,19 +914,19 @@ __device__ void warp_solve_e1(int N, const WarpBuf<LT> &b, double h, WVecT<Grp<L
   }
 #pragma unroll
   for (int r = 0; r < WR; ++r) res.v[r] = rhs.v[r] - fac1 * x.v[r] + res.v[r];
-  warp_solve_real<L, LT>(N, b.ld, b.E1, b.ip1, b.v1, res);
+  sys.solve_real(b, res);
 #pragma unroll
   for (int r = 0; r < WR; ++r) x.v[r] += res.v[r];
 }
 
-template <int L, typename LT, bool FDJ>
-__device__ bool warp_init(const MechView &m, const WarpBuf<LT> &b, double P,
-                          WStateT<Grp<L>::WR> &w, StepState &s, const RadauParams &p,
-                          int64_t idx) {
+template <int L, typename LT, bool FDJ, class Sys>
+__device__ bool warp_init_sys(const Sys &sys, const WarpBuf<LT> &b, double P,
+                              WStateT<Grp<L>::WR> &w, StepState &s, const RadauParams &p,
+                              int64_t idx) {
   constexpr int WR = Grp<L>::WR;
-  const int N = m.ns;
+  const int N = sys.n();
   init_state<64, LT>(s);
-  if (warp_chem<L, LT>(m, b, P, w.y, w.f0, !FDJ)) {
+  if (sys.chem(b, P, w.y, w.f0, !FDJ)) {
     s.status = 4;
     return true;
   }
@@ -906,9 +936,10 @@ __device__ bool warp_init(const MechView &m, const WarpBuf<LT> &b, double P,
     s.caljac = 1;
     s.need = NEED_LU;
   }
+  const int lane = Grp<L>::lane();
 #pragma unroll
   for (int r = 0; r < WR; ++r) {
-    w.scal.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
+    w.scal.v[r] = p.atol * sys.atol_w(lane + L * r) + p.rtol * fabs(w.y.v[r]);
     w.isc.v[r] = 1.0 / w.scal.v[r];
   }
   if (p.h0) {
@@ -917,13 +948,13 @@ __device__ bool warp_init(const MechView &m, const WarpBuf<LT> &b, double P,
     // starting-step heuristic (first_h0 / first_h1 with group norms)
     WVecT<WR> sc;
 #pragma unroll
-    for (int r = 0; r < WR; ++r) sc.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
+    for (int r = 0; r < WR; ++r) sc.v[r] = w.scal.v[r];
     const double d0 = wrms_w<L>(N, w.y, sc), d1 = wrms_w<L>(N, w.f0, sc);
     double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
     h0 = fmin(h0, p.dt);
 #pragma unroll
     for (int r = 0; r < WR; ++r) w.u.v[r] = w.y.v[r] + h0 * w.f0.v[r];
-    const int rc = warp_chem<L, LT>(m, b, P, w.u, w.fu, false);
+    const int rc = sys.chem(b, P, w.u, w.fu, false);
     s.nfcn++;
     if (rc != 0) {
       s.h = 0.01 * h0;
@@ -941,13 +972,13 @@ __device__ bool warp_init(const MechView &m, const WarpBuf<LT> &b, double P,
   return false;
 }
 
-template <int L, typename LT, bool FDJ>
-__device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
-                          WStateT<Grp<L>::WR> &w, StepState &s, const RadauParams &p,
-                          int64_t idx) {
+template <int L, typename LT, bool FDJ, class Sys>
+__device__ bool warp_step_sys(const Sys &sys, const WarpBuf<LT> &b, double P,
+                              WStateT<Grp<L>::WR> &w, StepState &s, const RadauParams &p,
+                              int64_t idx) {
   using G = Grp<L>;
   constexpr int WR = G::WR;
-  const int N = m.ns, lane = G::lane();
+  const int N = sys.n(), lane = G::lane();
   for (;;) {
     if (s.need == NEED_JAC) {
       int rc = 0;
@@ -962,7 +993,7 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
 #pragma unroll
           for (int r = 0; r < WR; ++r) w.u.v[r] = w.y.v[r];
           if (lane == (j & (L - 1))) slot_set<WR>(w.u, j / L, yj + inc);
-          rc |= warp_chem<L, LT>(m, b, P, w.u, w.fu, false);
+          rc |= sys.chem(b, P, w.u, w.fu, false);
 #pragma unroll
           for (int r = 0; r < WR; ++r) {
             const int i = lane + L * r;
@@ -972,7 +1003,7 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
         G::sync();
         s.nfcn += N;
       } else {
-        rc = warp_chem<L, LT>(m, b, P, w.y, w.fu, true);
+        rc = sys.chem(b, P, w.y, w.fu, true);
       }
       if (rc) {
         s.status = 4;
@@ -983,7 +1014,7 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
       s.need = NEED_LU;
     }
     if (s.need == NEED_LU) {
-      const int sing = warp_factor<L, LT>(N, b, s.h);
+      const int sing = sys.factor(b, s.h);
       s.ndec++;
       if (sing) {
         if (++s.nsing >= 5) {
@@ -1028,13 +1059,13 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
     int bad = 0;
 #pragma unroll
     for (int r = 0; r < WR; ++r) w.u.v[r] = w.y.v[r] + w.z1.v[r];
-    bad |= warp_chem<L, LT>(m, b, P, w.u, w.F1, false);
+    bad |= sys.chem(b, P, w.u, w.F1, false);
 #pragma unroll
     for (int r = 0; r < WR; ++r) w.u.v[r] = w.y.v[r] + w.z2.v[r];
-    bad |= warp_chem<L, LT>(m, b, P, w.u, w.F2, false);
+    bad |= sys.chem(b, P, w.u, w.F2, false);
 #pragma unroll
     for (int r = 0; r < WR; ++r) w.u.v[r] = w.y.v[r] + w.z3.v[r];
-    bad |= warp_chem<L, LT>(m, b, P, w.u, w.fu, false);
+    bad |= sys.chem(b, P, w.u, w.fu, false);
     s.nfcn += 3;
     if (bad) {
       outcome = 3;
@@ -1050,8 +1081,8 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
       w.z2.v[r] = g2 - (alphn * w.w2.v[r] - betan * w.w3.v[r]);
       w.z3.v[r] = g3 - (betan * w.w2.v[r] + alphn * w.w3.v[r]);
     }
-    warp_solve_real<L, LT>(N, b.ld, b.E1, b.ip1, b.v1, w.z1);
-    warp_solve_cplx<L, LT>(N, b.ld, b.E2r, b.E2i, b.ip2, b.v1, b.v2, w.z2, w.z3);
+    sys.solve_real(b, w.z1);
+    sys.solve_cplx(b, w.z2, w.z3);
     double sum = 0.0;
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
@@ -1098,19 +1129,19 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
     w.fe.v[r] = (RC.d[0] * w.z1.v[r] + RC.d[1] * w.z2.v[r] + RC.d[2] * w.z3.v[r]) * ih;
     w.u.v[r] = w.fe.v[r] + w.f0.v[r];
   }
-  warp_solve_e1<L, LT>(N, b, s.h, w.u);
+  warp_solve_e1<L, LT>(sys, b, s.h, w.u);
   double err = fmax(wrms_wi<L>(N, w.u, w.isc), 1e-10);
   if (err >= 1.0 && (s.first || s.reject)) {
 #pragma unroll
     for (int r = 0; r < WR; ++r) w.F2.v[r] = w.y.v[r] + w.u.v[r];
-    const int bad = warp_chem<L, LT>(m, b, P, w.F2, w.fu, false);
+    const int bad = sys.chem(b, P, w.F2, w.fu, false);
     s.nfcn++;
     if (bad) {
       err = 1e10;
     } else {
 #pragma unroll
       for (int r = 0; r < WR; ++r) w.u.v[r] = w.fu.v[r] + w.fe.v[r];
-      warp_solve_e1<L, LT>(N, b, s.h, w.u);
+      warp_solve_e1<L, LT>(sys, b, s.h, w.u);
       err = fmax(wrms_wi<L>(N, w.u, w.isc), 1e-10);
     }
   }
@@ -1138,12 +1169,12 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
     const double acont3 = (ak - z1 * RC.ic1) * RC.ic2;
     w.a2.v[r] = (ak - w.a1.v[r]) * RC.ic1m1;
     w.a3.v[r] = w.a2.v[r] - acont3;
-    w.scal.v[r] = p.atol + p.rtol * fabs(w.y.v[r]);
+    w.scal.v[r] = p.atol * sys.atol_w(lane + L * r) + p.rtol * fabs(w.y.v[r]);
     w.isc.v[r] = 1.0 / w.scal.v[r];
   }
   if (s.last || (p.stop_after > 0 && s.naccpt >= p.stop_after)) return true;
   const bool wantJ = !FDJ && s.theta > THET;
-  if (warp_chem<L, LT>(m, b, P, w.y, w.f0, wantJ)) {
+  if (sys.chem(b, P, w.y, w.f0, wantJ)) {
     s.status = 4;
     return true;
   }
@@ -1155,6 +1186,21 @@ __device__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
     if (s.need == NEED_JAC) s.need = NEED_LU;
   }
   return false;
+}
+
+// The mass-fraction reactor's drivers (k_integrate_lanes).
+template <int L, typename LT, bool FDJ>
+__device__ __forceinline__ bool warp_init(const MechView &m, const WarpBuf<LT> &b, double P,
+                                          WStateT<Grp<L>::WR> &w, StepState &s,
+                                          const RadauParams &p, int64_t idx) {
+  return warp_init_sys<L, LT, FDJ>(MassFracSys<L, LT>{&m}, b, P, w, s, p, idx);
+}
+
+template <int L, typename LT, bool FDJ>
+__device__ __forceinline__ bool warp_step(const MechView &m, const WarpBuf<LT> &b, double P,
+                                          WStateT<Grp<L>::WR> &w, StepState &s,
+                                          const RadauParams &p, int64_t idx) {
+  return warp_step_sys<L, LT, FDJ>(MassFracSys<L, LT>{&m}, b, P, w, s, p, idx);
 }
 
 }  // namespace kin

@@ -32,7 +32,8 @@ EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integra
            "kin_mlp_get_params", "kin_mlp_set_params", "kin_mlp_forward", "kin_mlp_grad",
            "kin_mlp_train_step", "kin_moments", "kin_mlp_features", "kin_mlp_targets",
            "kin_mlp_predict", "kin_autotune", "kin_order_states", "kin_mlp_train_step_rows",
-           "kin_resolve_options")
+           "kin_resolve_options", "kin_conc_analyse", "kin_conc_create", "kin_conc_destroy",
+           "kin_integrate_conc", "kin_conc_get_stats")
 
 
 class KinError(RuntimeError):
@@ -106,6 +107,11 @@ def lib():
             L.kin_mlp_targets.argtypes = [i32, vp, vp, i64, vp, vp, vp, vp]
             L.kin_mlp_predict.argtypes = [vp, i32, vp, vp, vp, i64, d, vp, vp, vp, vp, vp, vp,
                                           vp]
+            L.kin_conc_analyse.argtypes = [vp, vp, vp, vp]
+            L.kin_conc_create.argtypes = [vp, C.POINTER(vp)]
+            L.kin_conc_destroy.argtypes = [vp]
+            L.kin_integrate_conc.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp, vp, vp]
+            L.kin_conc_get_stats.argtypes = [vp, vp]
             L.kin_status_string.argtypes = [C.c_int]
             L.kin_status_string.restype = C.c_char_p
             _lib = L
@@ -350,6 +356,70 @@ class Mechanism:
         n = int(P.shape[0])
         _check(lib().kin_jacobian(self.handle, _ptr(y), _ptr(P), n, int(bool(fd)), float(h),
                                   _ptr(scal), _ptr(J), _stream(stream)), "kin_jacobian")
+
+
+def conc_analyse(mech):
+    """kin_conc_analyse (host only): (var [ns+1], filled pattern [(ns+1)^2] in
+    elimination order, counts [nnz J, nnz L+U, real LU ops, real solve ops])."""
+    d, keep = mech_desc(mech)
+    N = int(mech.ns) + 1
+    var = np.zeros(N, dtype=np.int32)
+    pat = np.zeros((N, N), dtype=np.uint8)
+    cnt = np.zeros(4, dtype=np.int64)
+    _check(lib().kin_conc_analyse(C.byref(d), var.ctypes.data, pat.ctypes.data, cnt.ctypes.data),
+           "kin_conc_analyse")
+    del keep
+    return var, pat.astype(bool), cnt
+
+
+class ConcMechanism:
+    """The concentration-based form of a mechanism with its sparse LU
+    structure, on the current CUDA device (kin_conc_create)."""
+
+    def __init__(self, mech):
+        self.ns, self.nr = int(mech.ns), int(mech.nr)
+        d, keep = mech_desc(mech)
+        h = C.c_void_p()
+        _check(lib().kin_conc_create(C.byref(d), C.byref(h)), "kin_conc_create")
+        del keep
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("plan destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.kin_conc_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, status=None, counters=None,
+                  stream=None, **opt):
+        """Advance device tensors Y [ns, n], T [n] in place over dt (kin_integrate_conc)."""
+        n = int(T.shape[0])
+        opt.setdefault("layout", "warp")
+        o = options(**opt)
+        rc = lib().kin_integrate_conc(self.handle, _ptr(Y), _ptr(T), _ptr(P), n, float(dt),
+                                      float(rtol), float(atol), C.byref(o), _ptr(status),
+                                      _ptr(counters), _stream(stream))
+        _check(rc, "kin_integrate_conc")
+
+    def stats(self):
+        """Totals of the last integration (kin_conc_get_stats)."""
+        out = np.zeros(9, dtype=np.int64)
+        rc = lib().kin_conc_get_stats(self.handle, out.ctypes.data)
+        if rc not in (KIN_OK, KIN_ERR_STATE_FAILED):
+            _check(rc, "kin_conc_get_stats")
+        keys = list(COUNTER_NAMES[:7]) + ["failed", "max_steps_state"]
+        return dict(zip(keys, out.tolist()))
 
 
 def radau_constants():

@@ -170,3 +170,30 @@ def test_conc_conversions_round_trip():
     Y, T = O.from_conc(mech, phi, st.P)
     np.testing.assert_array_equal(T, st.T)
     np.testing.assert_allclose(Y, st.Y, rtol=1e-13, atol=1e-17)
+
+
+def test_per_component_atol_is_a_change_of_variables():
+    """orc_opts.atol_scale (the moles' atol / W_k of the concentration form):
+    Radau with weights atol s_i + rtol |y_i| is Radau on z = y / s with the
+    scalar atol (the method is invariant under the scaling, and so are its
+    error and Newton norms).  Both runs take the same steps and agree to
+    rounding."""
+    mech = synth.make_mechanism("h2")
+    om = O.OracleMech(mech)
+    st = synth.make_states(mech, 2, seed=31, T_range=(1000.0, 1300.0))
+    s = np.concatenate([[1.0, 1.0], 1.0 / mech.W[:-1]])
+    for i in range(st.n):
+        P = st.P[i]
+        phi0 = O.to_conc(mech, st.Y[:, i], st.T[i], P)
+        f = lambda t, v: O.rhs_conc(om, P, v)[0]
+        J = lambda t, v: O.jac_conc(om, P, v)[0]
+        ya, sa = O.radau(f, J, phi0, 0.0, 1e-4, atol_scale=s)
+        fz = lambda t, z: f(t, z * s) / s
+        Jz = lambda t, z: J(t, z * s) * s[None, :] / s[:, None]
+        zb, sb = O.radau(fz, Jz, phi0 / s, 0.0, 1e-4)
+        assert sa["status"] == 0 and sb["status"] == 0
+        assert sa["nstep"] == sb["nstep"] and sa["naccpt"] == sb["naccpt"]
+        np.testing.assert_allclose(zb * s, ya, rtol=1e-9, atol=1e-18)
+        # and the scaling matters: the scalar atol on the moles takes fewer steps
+        yc, sc = O.radau(f, J, phi0, 0.0, 1e-4)
+        assert sc["nstep"] < sa["nstep"]
