@@ -75,12 +75,13 @@ def parse():
 # algorithmic operation counts (FP64 / FP32 flops per event)
 # ---------------------------------------------------------------------------
 
-def op_model(mech):
+def op_model(mech, form="massfrac"):
     """Counted operations per event for this mechanism (oracle/flop_counts.json,
     written by oracle/opcount.py; transcendentals count as one operation), or
-    None when the mechanism has no committed count."""
+    None when the mechanism has no committed count.  form "conc": the
+    concentration-based form with its sparse LU."""
     from oracle import opcount
-    rec = opcount.load_counts(mech)
+    rec = opcount.load_counts(mech, form)
     return None if rec is None else opcount.per_event(rec)
 
 
@@ -327,7 +328,9 @@ def run_ours(args, rank, world):
                       "h2d_bytes_per_step": int(n * (mech.ns + 2) * 8),
                       "d2h_bytes_per_step": int(n * (mech.ns + 1) * 8)}
     if rank == 0 and not args.no_extras and not args.no_config3 and args.workload == WORKLOAD:
-        out["configs"] = {"ch4_2p18": config3_leg(stream), "mlp_train": mlp_leg(stream)}
+        out["configs"] = {"ch4_2p18": config3_leg(stream),
+                          "ch4_2p18_conc": config3_leg(stream, form="conc"),
+                          "mlp_train": mlp_leg(stream)}
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -336,16 +339,19 @@ def run_ours(args, rank, world):
                 f64=f64, f32=f32, n=n, mech=mech, st=st, extras=out)
 
 
-def config3_leg(stream):
+def config3_leg(stream, form="massfrac"):
     """The CH4-like configuration at full size, outside the headline's timed
     region: 2^18 states (53 species, 325 reactions), dt = 1e-4 s, the state-
     per-warp layout with FP32 Newton matrices.  One warm-up launch on a 4096-
     state prefix, then one timed launch of the whole batch (CUDA events on the
-    launching stream, L2 flushed before), with its own counted roofline."""
+    launching stream, L2 flushed before), with its own counted roofline.
+    form "conc": the same states in the concentration-based form with its
+    sparse LU (kin_integrate_conc; Sec. 3.3, Sec. 4)."""
     import torch
     from paper_1607_03884_gb300 import kin, synth
     mech, st, _ = synth.workload("ch4_2p18")
-    mg = kin.Mechanism(mech)
+    conc = form == "conc"
+    mg = kin.ConcMechanism(mech) if conc else kin.Mechanism(mech)
     opt = dict(layout="warp", lanes=32, lu_fp32=True)
     Y, T, P = (torch.from_numpy(a.copy()).cuda() for a in (st.Y, st.T, st.P))
     m = 4096
@@ -364,13 +370,18 @@ def config3_leg(stream):
     clocks = clk.stop()
     sec = e0.elapsed_time(e1) / 1e3
     tot = mg.stats()
-    ops = op_model(mech)
+    ops = op_model(mech, form)
     f64, f32 = algorithmic_flops(tot, ops, True) if ops else (None, None)
-    return {"workload": "ch4_2p18", "states": st.n, "species": mech.ns, "reactions": mech.nr,
-            "dt": 1e-4, "layout": "warp", "lanes": 32, "newton_matrices": "fp32",
-            "value": st.n / sec, "unit": "states/s", "seconds": sec, "failed": tot["failed"],
-            "counters": {k: int(v) for k, v in tot.items()}, "clocks": clocks,
-            "roofline": roofline(f64, f32, sec, None, "k_integrate_lanes<32, float>")}
+    kernel = "k_integrate_conc<32, float>" if conc else "k_integrate_lanes<32, float>"
+    rec = {"workload": "ch4_2p18", "states": st.n, "species": mech.ns, "reactions": mech.nr,
+           "dt": 1e-4, "layout": "warp", "lanes": 32, "newton_matrices": "fp32",
+           "form": "concentration-based, sparse LU" if conc else "mass fractions, dense LU",
+           "value": st.n / sec, "unit": "states/s", "seconds": sec, "failed": tot["failed"],
+           "counters": {k: int(v) for k, v in tot.items()}, "clocks": clocks,
+           "roofline": roofline(f64, f32, sec, None, kernel)}
+    if conc:
+        rec["tolerances"] = "atol on T and V, atol / W_k on the moles n_k (the mass-fraction weights)"
+    return rec
 
 
 def mlp_leg(stream, rows=1 << 16, steps=20):
@@ -557,7 +568,8 @@ def roofline(f64, f32, seconds, traffic=None, kernel=None):
             "time_bound_frac": a64 / FP64_PEAK_TFLOPS + f32 / seconds / 1e12 / FP32_PEAK_TFLOPS,
             "flops_source": "operations per event counted by oracle/opcount.py "
                             "(oracle/flop_counts.json) times the launch's event counters",
-            "traffic_source": "ncu dram__bytes_read+write of a 131072-state capture "
+            "traffic_source": None if traffic is None else
+                              "ncu dram__bytes_read+write of a 131072-state capture "
                               "(profiles/dram_traffic.json), scaled by states"}
 
 

@@ -22,7 +22,10 @@ Sec. 2.1, written with per-reaction loops over the participating species):
 - the LU factorisations of (gamma/h) I - J and ((alpha + i beta)/h) I - J
   with partial pivoting, and their solves;
 - the vector algebra of one simplified-Newton iteration, of one error
-  estimate and of one step (Hairer & Wanner IV.8, the method of Sec. 2.1).
+  estimate and of one step (Hairer & Wanner IV.8, the method of Sec. 2.1);
+- the same events of the concentration-based form (Sec. 3.3, Sec. 4: the
+  reactor in phi = [T, V, n_k], its Jacobian, and the LU over the sparse
+  pattern in a minimum-degree order, computed here).
 The tests hold rhs/jac to the oracle's orc_rhs/orc_jac values (so the counted
 code evaluates the same functions) and the LU/solve counts to their closed
 forms.  Per-mechanism tables (log A, NASA-7 coefficients divided by their
@@ -292,6 +295,47 @@ def _acc(acc, nu, x):
     return acc + x if nu == 1 else acc - x if nu == -1 else acc + nu * x
 
 
+def _reaction_rates(tb, T, logT, invT, lnPf, C, g, Ctot, want_jac):
+    """Net rates q_i of every reaction at (T, C) gathered into the production
+    rates wd[k] (None for a species no reaction changes), with the per-reaction
+    quantities the Jacobians need (rx)."""
+    nr, ns = tb.nr, tb.ns
+    wd = [None] * ns
+    rx = []
+    for i in range(nr):
+        lnkf = tb.lnA[i] + tb.b[i] * logT - tb.Th[i] * invT
+        kf = exp(lnkf)
+        lnKc = tb.dnu[i] * lnPf if tb.dnu[i] != 0 else None
+        for s in tb.prod[i]:
+            lnKc = g[s] if lnKc is None else lnKc + g[s]
+        for s in tb.reac[i]:
+            lnKc = -g[s] if lnKc is None else lnKc - g[s]
+        kr = kf * exp(-lnKc)
+        fwd = C[tb.reac[i][0]]
+        for s in tb.reac[i][1:]:
+            fwd = fwd * C[s]
+        rev = C[tb.prod[i][0]]
+        for s in tb.prod[i][1:]:
+            rev = rev * C[s]
+        phi, dphi_dT, dphi_dM, M = 1.0, 0.0, 0.0, None
+        dlnkf = None
+        if tb.type[i] != 0:
+            M = Ctot
+            for k, e in tb.eff[i]:
+                M = M + e * C[k]
+            if tb.type[i] == 1:
+                phi, dphi_dM = M, 1.0
+            else:
+                dlnkf = tb.b[i] * invT + tb.Th[i] * (invT * invT)
+                phi, dphi_dT, dphi_dM = _troe(tb.troe[i], T, logT, invT, kf, dlnkf, M, want_jac)
+        Rn = kf * fwd - kr * rev
+        q = Rn if tb.type[i] == 0 else phi * Rn
+        for k, nu in tb.nu[i].items():
+            wd[k] = _acc(wd[k], nu, q)
+        rx.append((kf, kr, fwd, rev, phi, dphi_dT, dphi_dM, M, Rn, dlnkf))
+    return wd, rx
+
+
 def evaluate(tb: Tables, P, y, want_jac=False):
     """f(y) (list of N values) and, with want_jac, the analytical Jacobian
     J[r][c] = df_r/dy_c at the same point, y = [T, Y_0 .. Y_{ns-2}].
@@ -343,39 +387,7 @@ def evaluate(tb: Tables, P, y, want_jac=False):
             t2 = Yall[k] * d * tb.invW[k]
             dcpm = t2 if dcpm is None else dcpm + t2
     Ctot = rho * S
-    wd = [None] * ns
-    rx = []
-    for i in range(nr):
-        lnkf = tb.lnA[i] + tb.b[i] * logT - tb.Th[i] * invT
-        kf = exp(lnkf)
-        lnKc = tb.dnu[i] * lnPf if tb.dnu[i] != 0 else None
-        for s in tb.prod[i]:
-            lnKc = g[s] if lnKc is None else lnKc + g[s]
-        for s in tb.reac[i]:
-            lnKc = -g[s] if lnKc is None else lnKc - g[s]
-        kr = kf * exp(-lnKc)
-        fwd = C[tb.reac[i][0]]
-        for s in tb.reac[i][1:]:
-            fwd = fwd * C[s]
-        rev = C[tb.prod[i][0]]
-        for s in tb.prod[i][1:]:
-            rev = rev * C[s]
-        phi, dphi_dT, dphi_dM, M = 1.0, 0.0, 0.0, None
-        dlnkf = None
-        if tb.type[i] != 0:
-            M = Ctot
-            for k, e in tb.eff[i]:
-                M = M + e * C[k]
-            if tb.type[i] == 1:
-                phi, dphi_dM = M, 1.0
-            else:
-                dlnkf = tb.b[i] * invT + tb.Th[i] * (invT * invT)
-                phi, dphi_dT, dphi_dM = _troe(tb.troe[i], T, logT, invT, kf, dlnkf, M, want_jac)
-        Rn = kf * fwd - kr * rev
-        q = Rn if tb.type[i] == 0 else phi * Rn
-        for k, nu in tb.nu[i].items():
-            wd[k] = _acc(wd[k], nu, q)
-        rx.append((kf, kr, fwd, rev, phi, dphi_dT, dphi_dM, M, Rn, dlnkf))
+    wd, rx = _reaction_rates(tb, T, logT, invT, lnPf, C, g, Ctot, want_jac)
     Hw = None
     for k in range(inn):
         if wd[k] is None:
@@ -726,6 +738,341 @@ def accept_algebra(N):
 
 
 # ---------------------------------------------------------------------------
+# The concentration-based form (Sec. 3.3, Sec. 4) and its sparse LU
+# ---------------------------------------------------------------------------
+
+def evaluate_conc(tb: Tables, P, phi, want_jac=False):
+    """f(phi) and, with want_jac, J of the concentration-based form,
+    phi = [T, V, n_0 .. n_{ns-2}] per unit mass (oracle/chem.c orc_rhs_conc):
+    C_k = n_k / V, Ctot = P / (Ru T), C_in = Ctot - sum C_k; the same rates;
+    dT/dt = -T sum h_k wdot_k / sum C_k cp_k, dV/dt = V (sum wdot / Ctot +
+    (dT/dt) / T), dn_k/dt = V wdot_k.  J per reaction: dq/dn_l = (mass-action
+    partial + u eff'_l) / V, dq/dV = -sigma / V, dq/dT at fixed phi; the T and
+    V rows by the quotient rule over column sums of the species block."""
+    ns, inn = tb.ns, tb.inert
+    T, V = phi[0], phi[1]
+    iV = 1.0 / V
+    C = [phi[2 + k] * iV for k in range(inn)]
+    sC = C[0]
+    for c in C[1:]:
+        sC = sC + c
+    Ctot = P / (RU * T)
+    C.append(Ctot - sC)
+    logT = log(T)
+    invT = 1.0 / T
+    lnPf = tb.ln_patm_ru - logT
+    hs, g, cpk, dcp = [], [], [], []
+    Cs = dCsT = None
+    for k in range(ns):
+        r = 0 if float(T) < tb.Tmid[k] else 1
+        cp = _horner(tb.cp[k][r], T)
+        hc = tb.h[k][r]
+        hs.append(_horner(hc[:5], T) + hc[5] * invT)
+        gc = tb.g[k][r]
+        g.append(gc[0] * logT + T * _horner(gc[1:5], T) + gc[5] + gc[6] * invT)
+        cpk.append(cp)
+        t = C[k] * cp
+        Cs = t if Cs is None else Cs + t
+        if want_jac:
+            c = tb.cp[k][r]
+            d = c[1] + T * (2.0 * c[2] + T * (3.0 * c[3] + T * (4.0 * c[4])))
+            dcp.append(d)
+            t2 = C[k] * d
+            dCsT = t2 if dCsT is None else dCsT + t2
+    wd, rx = _reaction_rates(tb, T, logT, invT, lnPf, C, g, Ctot, want_jac)
+    Hs = Ws = None
+    for k in range(inn):
+        if wd[k] is None:
+            continue
+        t = hs[k] * wd[k]
+        Hs = t if Hs is None else Hs + t
+        Ws = wd[k] if Ws is None else Ws + wd[k]
+    fT = -(T * Hs) / Cs
+    fV = V * (Ws / Ctot + fT * invT)
+    f = [fT, fV] + [V * wd[k] if wd[k] is not None else 0.0 for k in range(inn)]
+    if not want_jac:
+        return f, None
+    return f, _jacobian_conc(tb, T, V, iV, invT, C, sC, Ctot, hs, cpk, Cs, dCsT, wd, rx, fT,
+                             Ws)
+
+
+def _jacobian_conc(tb, T, V, iV, invT, C, sC, Ctot, hs, cpk, Cs, dCsT, wd, rx, fT, Ws):
+    ns, inn = tb.ns, tb.inert
+    N = ns + 1
+    Jn = [dict() for _ in range(inn)]
+    B, Tc = [None] * inn, [None] * inn
+    for i, (kf, kr, fwd, rev, phi, dphi_dT, dphi_dM, M, Rn, dlnkf) in enumerate(rx):
+        reac, prod = tb.reac[i], tb.prod[i]
+        typ = tb.type[i]
+        pkf = kf if typ == 0 else phi * kf
+        pkr = kr if typ == 0 else phi * kr
+        D = {}
+        for side, coef, sl in ((0, pkf, reac), (1, pkr, prod)):
+            for a, sp in enumerate(sl):
+                d = coef
+                for b2, other in enumerate(sl):
+                    if b2 != a:
+                        d = d * C[other]
+                D[sp] = (d if side == 0 else -d) if sp not in D else \
+                    (D[sp] + d if side == 0 else D[sp] - d)
+        u = None
+        if typ != 0:
+            u = Rn * dphi_dM
+            for k, e in tb.eff[i]:
+                t = u * e
+                D[k] = t if k not in D else D[k] + t
+        nre, npr = len(reac), len(prod)
+        sig = pkf * fwd if nre == 1 else (nre * pkf) * fwd
+        sig = sig - (pkr * rev if npr == 1 else (npr * pkr) * rev)
+        if typ != 0:
+            sig = sig + u * (M - Ctot)
+        dlnkf_i = dlnkf if dlnkf is not None else tb.b[i] * invT + tb.Th[i] * (invT * invT)
+        dH = None
+        for sp in prod:
+            dH = hs[sp] if dH is None else dH + hs[sp]
+        for sp in reac:
+            dH = -hs[sp] if dH is None else dH - hs[sp]
+        dlnkr = dlnkf_i - (dH - tb.dnu[i]) * invT if tb.dnu[i] != 0 else dlnkf_i - dH * invT
+        dq = (kf * dlnkf_i) * fwd - (kr * dlnkr) * rev
+        if typ != 0:
+            dq = phi * dq
+        if typ == 2:
+            dq = dq + Rn * dphi_dT
+        if typ != 0:
+            dq = dq - u * Ctot * invT
+        for k, nu in tb.nu[i].items():
+            row = Jn[k]
+            for j, x in D.items():
+                row[j] = _acc(row.get(j), nu, x)
+            B[k] = _acc(B[k], nu, sig)
+            Tc[k] = _acc(Tc[k], nu, dq)
+    J = [[0.0] * N for _ in range(N)]
+    sHB = sHT = sCW = sB = sTc = sCC = None
+
+    def add(acc, x):
+        return x if acc is None else acc + x
+    for k in range(inn):
+        if Tc[k] is not None:
+            J[2 + k][0] = V * Tc[k]
+            sHT = add(sHT, hs[k] * Tc[k])
+            sTc = add(sTc, Tc[k])
+        if B[k] is not None or wd[k] is not None:
+            J[2 + k][1] = (wd[k] - B[k]) if B[k] is not None else wd[k]
+        if B[k] is not None:
+            sHB = add(sHB, hs[k] * B[k])
+            sB = add(sB, B[k])
+        if wd[k] is not None:
+            sCW = add(sCW, cpk[k] * wd[k])
+        sCC = add(sCC, cpk[k] * C[k])
+        for j, x in Jn[k].items():
+            J[2 + k][2 + j] = x
+    cp_in = cpk[inn]
+    for c in range(N):
+        if c >= 2:
+            l = c - 2
+            sh = sw = None
+            for k in range(inn):
+                x = Jn[k].get(l)
+                if x is not None:
+                    sh = add(sh, hs[k] * x)
+                    sw = add(sw, x)
+            dTH = T * iV * sh if sh is not None else 0.0
+            dCs = (cpk[l] - cp_in) * iV
+            dWs = sw if sw is not None else 0.0
+        elif c == 1:
+            dTH = -(T * iV * sHB)
+            dCs = (cp_in * sC - sCC) * iV
+            dWs = -sB
+        else:
+            dTH = sCW + T * sHT
+            dCs = dCsT - cp_in * Ctot * invT
+            dWs = V * sTc
+        jt = -(dTH + fT * dCs) / Cs
+        jv = dWs / Ctot + V * jt * invT
+        if c == 1:
+            jv = jv + (Ws / Ctot + fT * invT)
+        if c == 0:
+            jv = jv + V * (Ws / (Ctot * T) - fT * invT * invT)
+        J[0][c] = jt
+        J[1][c] = jv
+    return J
+
+
+def conc_state(mech, Y, T, P):
+    """phi = [T, V, n_0 .. n_{ns-2}] per unit mass of a state (Y full)."""
+    W = np.asarray(mech.W, dtype=float)
+    nk = np.asarray(Y, dtype=float) / W
+    return np.concatenate([[T, RU * T * nk.sum() / P], nk[:-1]])
+
+
+def conc_structure(mech):
+    """Elimination order and filled pattern of the concentration-based Newton
+    matrices, computed here: J's pattern in phi order (full T and V rows and
+    columns; species coupled through a shared reaction or a non-default
+    collision efficiency), the species by minimum degree of the symmetric
+    species graph (ties to the lower index), T and V last, and the fill of
+    Gaussian elimination without pivoting.  Returns (var, pattern)."""
+    ns, nr, inn = int(mech.ns), int(mech.nr), int(mech.ns) - 1
+    N = ns + 1
+    S = np.eye(N, dtype=bool)
+    S[:2, :] = True
+    S[:, :2] = True
+    for i in range(nr):
+        sps = [int(x) for x in mech.reac[i] if x >= 0] + [int(x) for x in mech.prod[i] if x >= 0]
+        cols = set(sps)
+        if int(mech.rtype[i]) != 0:
+            cols |= {k for k in range(inn) if float(mech.eff[i][k]) != 1.0}
+        for r in sps:
+            for c in cols:
+                S[2 + r, 2 + c] = True
+    G = S[2:, 2:] | S[2:, 2:].T
+    np.fill_diagonal(G, False)
+    alive = list(range(inn))
+    order = []
+    while alive:
+        best = min(alive, key=lambda a: (int(sum(G[a, b] for b in alive)), a))
+        nb = [b for b in alive if G[best, b] and b != best]
+        for a in nb:
+            for b in nb:
+                if a != b:
+                    G[a, b] = True
+        alive.remove(best)
+        order.append(2 + best)
+    var = order + [0, 1]
+    P = S[np.ix_(var, var)].copy()
+    for k in range(N):
+        for i in range(k + 1, N):
+            if P[i, k]:
+                P[i, k + 1:] |= P[k, k + 1:]
+    return var, P
+
+
+def lu_sparse_real(a, pat):
+    """LU without pivoting over the pattern (multipliers by division)."""
+    n = len(a)
+    for k in range(n):
+        rows = [i for i in range(k + 1, n) if pat[i, k]]
+        cols = [j for j in range(k + 1, n) if pat[k, j]]
+        for i in rows:
+            l = a[i][k] / a[k][k]
+            a[i][k] = l
+            for j in cols:
+                a[i][j] = a[i][j] - l * a[k][j]
+
+
+def lu_sparse_cplx(a, pat):
+    n = len(a)
+    for k in range(n):
+        rows = [i for i in range(k + 1, n) if pat[i, k]]
+        cols = [j for j in range(k + 1, n) if pat[k, j]]
+        for i in rows:
+            l = _cdiv(a[i][k], a[k][k])
+            a[i][k] = l
+            for j in cols:
+                t = _cmul(l, a[k][j])
+                a[i][j] = (a[i][j][0] - t[0], a[i][j][1] - t[1])
+
+
+def solve_sparse_real(lu, pat, b):
+    n = len(lu)
+    b = list(b)
+    for i in range(n):
+        for j in range(i):
+            if pat[i, j]:
+                b[i] = b[i] - lu[i][j] * b[j]
+    for i in range(n - 1, -1, -1):
+        for j in range(i + 1, n):
+            if pat[i, j]:
+                b[i] = b[i] - lu[i][j] * b[j]
+        b[i] = b[i] / lu[i][i]
+    return b
+
+
+def solve_sparse_cplx(lu, pat, b):
+    n = len(lu)
+    b = list(b)
+    for i in range(n):
+        for j in range(i):
+            if pat[i, j]:
+                t = _cmul(lu[i][j], b[j])
+                b[i] = (b[i][0] - t[0], b[i][1] - t[1])
+    for i in range(n - 1, -1, -1):
+        for j in range(i + 1, n):
+            if pat[i, j]:
+                t = _cmul(lu[i][j], b[j])
+                b[i] = (b[i][0] - t[0], b[i][1] - t[1])
+        b[i] = _cdiv(b[i], lu[i][i])
+    return b
+
+
+def sparse_closed_forms(pat):
+    """Operation counts of the sparse routines above: per pivot k with l_k
+    multipliers and u_k update columns, real l_k + 2 l_k u_k and complex
+    11 l_k + 8 l_k u_k; a solve 2 (or 8) per off-diagonal entry of the
+    pattern and n (or 11 n) for the divisions."""
+    n = pat.shape[0]
+    l = [int(pat[k + 1:, k].sum()) for k in range(n)]
+    u = [int(pat[k, k + 1:].sum()) for k in range(n)]
+    off = int(pat.sum()) - n
+    return dict(lu_real=sum(a + 2 * a * b for a, b in zip(l, u)),
+                lu_cplx=sum(11 * a + 8 * a * b for a, b in zip(l, u)),
+                solve_real=2 * off + n, solve_cplx=8 * off + 11 * n)
+
+
+def count_conc(mech, phis, P):
+    """Operation counts per event of the concentration-based form with its
+    sparse LU (the record count_mechanism returns for the mass-fraction form)."""
+    tb = Tables(mech)
+    N = tb.ns + 1
+    rhs, jac = [], []
+    for i in range(phis.shape[1]):
+        y = [F(v) for v in phis[:, i]]
+        with counting() as t1:
+            evaluate_conc(tb, P[i], y)
+        with counting() as t2:
+            evaluate_conc(tb, P[i], y, want_jac=True)
+        rhs.append(t1.as_dict())
+        jac.append({k: t2.c[k] - t1.c[k] for k in KINDS})
+    if any(r != rhs[0] for r in rhs) or any(j != jac[0] for j in jac):
+        raise RuntimeError("concentration-form count depends on the state")
+    out = dict(N=N, digest=mech_digest(mech))
+    out["rhs"] = rhs[0]
+    jx = jac[0]
+    out["jac_beyond_rhs"] = dict(jx, flops=jx["add"] + jx["mul"] + jx["div"],
+                                 transcendentals=sum(jx[k] for k in KINDS[3:]))
+    var, pat = conc_structure(mech)
+    rng = np.random.default_rng(0)
+    Mx = np.where(pat, rng.normal(size=(N, N)), 0.0) + N * np.eye(N)
+    with counting() as tlu:
+        a = [[F(v) for v in row] for row in Mx]
+        lu_sparse_real(a, pat)
+    with counting() as tcl:
+        ac = [[(F(v), F(0.5 * v)) for v in row] for row in Mx]
+        lu_sparse_cplx(ac, pat)
+    with counting() as tsr:
+        solve_sparse_real(a, pat, [F(v) for v in rng.normal(size=N)])
+    with counting() as tsc:
+        solve_sparse_cplx(ac, pat, [(F(v), F(-v)) for v in rng.normal(size=N)])
+    with counting() as tbuild:
+        hh = F(1e-7)
+        _ = (1.0 / hh, 2.0 / hh, 3.0 / hh)
+        for i in range(N):
+            _ = (F(1.0) - a[i][i], F(1.0) - a[i][i])
+    out["lu_real"] = tlu.as_dict()
+    out["lu_cplx"] = tcl.as_dict()
+    out["matrix_build"] = tbuild.as_dict()
+    out["solve_real"] = tsr.as_dict()
+    out["solve_cplx"] = tsc.as_dict()
+    out["newton_algebra"] = newton_iteration_algebra(N).as_dict()
+    out["error_algebra"] = error_estimate_algebra(N).as_dict()
+    out["step_algebra"] = step_algebra(N).as_dict()
+    out["accept_algebra"] = accept_algebra(N).as_dict()
+    out["closed_forms"] = sparse_closed_forms(pat)
+    out["order"] = [int(v) for v in var]
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Per-mechanism record
 # ---------------------------------------------------------------------------
 
@@ -801,8 +1148,9 @@ def per_event(rec):
         step=w(rec["step_algebra"]), accept=w(rec["accept_algebra"]))
 
 
-def load_counts(mech):
-    """The committed record for this mechanism (flop_counts.json), or None."""
+def load_counts(mech, form="massfrac"):
+    """The committed record for this mechanism (flop_counts.json), or None;
+    form "conc": the concentration-based form's record."""
     try:
         with open(COUNTS_PATH) as fh:
             recs = json.load(fh)
@@ -811,7 +1159,7 @@ def load_counts(mech):
     d = mech_digest(mech)
     for rec in recs.get("mechanisms", {}).values():
         if rec.get("digest") == d:
-            return rec
+            return rec if form == "massfrac" else rec.get("conc")
     return None
 
 
@@ -826,6 +1174,11 @@ def main():
         y = np.concatenate([st.T[None], st.Y[:-1]])
         recs[kind] = count_mechanism(mech, y, st.P)
         recs[kind]["per_event"] = per_event(recs[kind])
+        phis = np.stack([conc_state(mech, st.Y[:, i], st.T[i], st.P[i]) for i in range(st.n)],
+                        axis=1)
+        cc = count_conc(mech, phis, st.P)
+        cc["per_event"] = per_event(cc)
+        recs[kind]["conc"] = cc
     doc = {"about": "operation counts per event of the Radau IIA path, counted by "
                     "oracle/opcount.py (python -m oracle.opcount); flops = add + mul + div, "
                     "transcendentals separate; per_event adds each transcendental as one",
@@ -834,7 +1187,7 @@ def main():
         json.dump(doc, fh, indent=1, sort_keys=True)
         fh.write("\n")
     for kind, rec in recs.items():
-        print(kind, rec["per_event"])
+        print(kind, rec["per_event"], "conc", rec["conc"]["per_event"])
 
 
 if __name__ == "__main__":

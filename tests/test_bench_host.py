@@ -26,8 +26,14 @@ def test_committed_counts_are_reproduced_and_used():
         y = np.concatenate([st.T[None], st.Y[:-1]])
         fresh = opcount.count_mechanism(mech, y, st.P)
         fresh["per_event"] = opcount.per_event(fresh)
+        phis = np.stack([opcount.conc_state(mech, st.Y[:, i], st.T[i], st.P[i])
+                         for i in range(st.n)], axis=1)
+        conc = opcount.count_conc(mech, phis, st.P)
+        conc["per_event"] = opcount.per_event(conc)
+        fresh["conc"] = conc
         assert doc["mechanisms"][kind] == json.loads(json.dumps(fresh)), kind
         assert bench.op_model(mech) == fresh["per_event"]
+        assert bench.op_model(mech, form="conc") == conc["per_event"]
     other = synth.make_mechanism("h2", seed=999)
     assert bench.op_model(other) is None
 
