@@ -61,6 +61,9 @@ def parse():
                    help="skip the full-size CH4-like and predictor legs among the extras")
     p.add_argument("--config5", action="store_true",
                    help="only the learned part at full size (2^20 training and test states)")
+    p.add_argument("--config3-only", default=None, choices=["massfrac", "conc"],
+                   help="time only configuration 3 in the given form (states = --n, default "
+                        "2^18)")
     p.add_argument("--mlp-only", action="store_true",
                    help="time only the predictor's training step (rows = --n, default 2^16)")
     p.add_argument("--cpu-sample", type=int, default=2048)
@@ -339,22 +342,25 @@ def run_ours(args, rank, world):
                 f64=f64, f32=f32, n=n, mech=mech, st=st, extras=out)
 
 
-def config3_leg(stream, form="massfrac"):
+def config3_leg(stream, form="massfrac", n=0):
     """The CH4-like configuration at full size, outside the headline's timed
     region: 2^18 states (53 species, 325 reactions), dt = 1e-4 s, the state-
     per-warp layout with FP32 Newton matrices.  One warm-up launch on a 4096-
     state prefix, then one timed launch of the whole batch (CUDA events on the
     launching stream, L2 flushed before), with its own counted roofline.
     form "conc": the same states in the concentration-based form with its
-    sparse LU (kin_integrate_conc; Sec. 3.3, Sec. 4)."""
+    sparse LU (kin_integrate_conc; Sec. 3.3, Sec. 4).  n > 0: the first n
+    states only."""
     import torch
     from paper_1607_03884_gb300 import kin, synth
     mech, st, _ = synth.workload("ch4_2p18")
+    if 0 < n < st.n:
+        st = st.subset(np.arange(n))
     conc = form == "conc"
     mg = kin.ConcMechanism(mech) if conc else kin.Mechanism(mech)
     opt = dict(layout="warp", lanes=32, lu_fp32=True)
     Y, T, P = (torch.from_numpy(a.copy()).cuda() for a in (st.Y, st.T, st.P))
-    m = 4096
+    m = min(4096, st.n)
     mg.integrate(Y[:, :m].contiguous(), T[:m].clone(), P[:m].contiguous(), 1e-4, RTOL, ATOL,
                  stream=stream, **opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -578,6 +584,10 @@ def main():
     if args.config5:    # the learned part at full size (minutes; not part of the default run)
         import torch
         print(json.dumps(config5_leg(torch.cuda.current_stream())))
+        return
+    if args.config3_only:   # configuration 3 alone, in one form (for profiling its kernel)
+        import torch
+        print(json.dumps(config3_leg(torch.cuda.current_stream(), args.config3_only, args.n)))
         return
     if args.mlp_only:   # the predictor's training step alone (for profiling its GEMMs)
         import torch

@@ -79,16 +79,17 @@ def test_thermo_fits_are_monotone_in_range(kind, h2_mech, ch4_mech):
 
 
 def test_structure_of_a_concentration_based_jacobian():
-    """The design's reason for not building a sparse, concentration-based
-    Jacobian with a sparse LU (the paper's proposed next step, Sec. 3.3 and
-    Sec. 4): in the state [T, V, n_0 .. n_{ns-2}] (extensive moles, constant
-    pressure, inert bath of efficiency 1) the Newton matrix couples two
-    species only through a shared reaction or a non-default collision
-    efficiency, with full T and V rows and columns.  On the seeded
-    mechanisms that structure is dense: the 13-species one fills 97 % of
-    its 14 x 14 matrix, the 53-species one 74 % of 54 x 54, and an LU in a
-    minimum-degree order fills 90 % or more, so a sparse LU saves at most a
-    tenth of the dense work."""
+    """How sparse the seeded mechanisms' concentration-based Newton matrices
+    are (the paper's proposed reformulation, Sec. 3.3 and Sec. 4): in the
+    state [T, V, n_0 .. n_{ns-2}] (extensive moles, constant pressure, inert
+    bath of efficiency 1) two species are coupled only through a shared
+    reaction or a non-default collision efficiency, with full T and V rows
+    and columns.  The seeded mechanisms pair species at random, so the
+    structure is dense: the 13-species one fills 97 % of its 14 x 14
+    matrix, the 53-species one 74 % of 54 x 54, and an LU in a minimum-
+    degree order (scipy's, here) fills 90 % or more.  The sparse LU's saving
+    is therefore in its first pivots (a sixth of the factorisation's
+    operations on CH4)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spl
     dens = {}
