@@ -333,6 +333,7 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.no_extras and not args.no_config3 and args.workload == WORKLOAD:
         out["configs"] = {"ch4_2p18": config3_leg(stream),
                           "ch4_2p18_conc": config3_leg(stream, form="conc"),
+                          "h2_exprb43": exprb_leg(stream),
                           "mlp_train": mlp_leg(stream)}
     if dist is not None:
         dist.barrier()
@@ -388,6 +389,44 @@ def config3_leg(stream, form="massfrac", n=0):
     if conc:
         rec["tolerances"] = "atol on T and V, atol / W_k on the moles n_k (the mass-fraction weights)"
     return rec
+
+
+def exprb_leg(stream, n=1 << 16, dt=1e-4, kappa=0.1):
+    """exprb43 with Krylov phi-function products (kin_integrate_exprb; the
+    paper's comparison method, Sec. 2.1, Sec. 3.1) on the first n states of
+    the headline workload, outside the headline's timed region: one warm-up
+    launch on 256 states, one timed launch (CUDA events, L2 flushed
+    before).  Its matrix-function work depends on per-call scaling counts
+    the counters do not record, so the leg reports no roofline."""
+    import torch
+    from paper_1607_03884_gb300 import kin, synth
+    mech, st, _ = synth.workload(WORKLOAD)
+    st = st.subset(np.arange(n))
+    xr = kin.ExpRosenbrock(mech)
+    Y, T, P = (torch.from_numpy(a.copy()).cuda() for a in (st.Y, st.T, st.P))
+    m = 256
+    xr.integrate(Y[:, :m].contiguous(), T[:m].clone(), P[:m].contiguous(), dt, RTOL, ATOL,
+                 kappa=kappa, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush.zero_()
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    xr.integrate(Y, T, P, dt, RTOL, ATOL, kappa=kappa, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = clk.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    tot = xr.stats()
+    return {"workload": f"{WORKLOAD} (first {n} states)", "states": n, "dt": dt,
+            "method": "exprb43, Krylov tolerance kappa = %g, one state per warp, FP64" % kappa,
+            "value": n / sec, "unit": "states/s", "seconds": sec, "failed": tot["failed"],
+            "steps_per_state": tot["nstep"] / n,
+            "krylov_dim_per_space": tot["krylov_dim"] / max(1, tot["krylov_spaces"]),
+            "counters": {k: int(v) for k, v in tot.items()}, "clocks": clocks,
+            "roofline": None}
 
 
 def mlp_leg(stream, rows=1 << 16, steps=20):

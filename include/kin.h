@@ -409,6 +409,72 @@ int kin_integrate_conc(kin_conc *c, double *Y, double *T, const double *P, int64
 int kin_conc_get_stats(kin_conc *c, int64_t *out);
 
 /* ---------------------------------------------------------------------------
+ * exprb43: the fourth-order exponential Rosenbrock method the paper runs
+ * beside Radau IIA (Sec. 2.1, Table of solvers; Sec. 3.1), for the same
+ * mass-fraction reactor and analytical Jacobian.  With g(u) = F(u) - J_n u
+ * and D_i = g(U_i) - g(u_n):
+ *   U2 = u_n + h/2 phi1(h/2 J) F(u_n),  U3 = u_n + h phi1(h J) (F(u_n) + D2),
+ *   u_{n+1} = u_n + h phi1(h J) F(u_n) + h (16 phi3 - 48 phi4)(h J) D2
+ *             + h (-2 phi3 + 12 phi4)(h J) D3,
+ * with the embedded third-order solution (16 phi3 D2 - 2 phi3 D3) for the
+ * step-size control (Hairer-Norsett-Wanner: weights atol + rtol max(|u_n|,
+ * |u_{n+1}|), h min(5, max(0.2, 0.9 err^-1/4)), no growth right after a
+ * rejection; a non-finite stage halves h).  J_n is evaluated at every new
+ * point.  The phi-function products come from one Krylov space per vector
+ * (Arnoldi), grown until Saad's leading error term of every product taken
+ * from it is at most kappa in the step's error weights (kappa = 0: the
+ * whole space), and phi_k of the small Hessenberg matrix from the
+ * exponential of an augmented matrix (scaling and squaring, Pade (6,6)).
+ * One state per warp; ns <= 57.
+ * ------------------------------------------------------------------------- */
+typedef struct kin_exprb kin_exprb;
+
+/* Build the tables and the per-warp workspace (basis, Hessenberg and
+ * matrix-function work, about 8 (ns+7)^2 doubles per resident warp) on the
+ * current device.  Errors: those of kin_mech_create; KIN_ERR_UNSUPPORTED
+ * for ns > 57. */
+int kin_exprb_create(const kin_mech_desc *desc, kin_exprb **out);
+
+/* Free (NULL is ignored; no work may be in flight). */
+void kin_exprb_destroy(kin_exprb *x);
+
+/* Advance n states over dt: Y dev [ns][n], T dev [n] in/out, P dev [n];
+ * tolerances as given (no transform); kappa >= 0 the Krylov tolerance;
+ * h0 dev [n] first steps or NULL (the starting-step heuristic); max_steps
+ * >= 1 per state.  status dev [n] (KIN_STATE_OK, _MAX_STEPS, _H_UNDERFLOW,
+ * _NONFINITE) and counters dev [8][n] or NULL: steps, accepted, rejected,
+ * right-hand sides, Jacobians, Krylov spaces built, their summed dimension,
+ * status.  Errors: KIN_ERR_INVALID_ARG (NULL with n > 0, n < 0, dt, rtol or
+ * atol not positive, kappa negative, max_steps < 1, another device).
+ * Asynchronous on stream; calls on one kin_exprb must not overlap. */
+int kin_integrate_exprb(kin_exprb *x, double *Y, double *T, const double *P, int64_t n,
+                        double dt, double rtol, double atol, double kappa, const double *h0,
+                        int32_t max_steps, int32_t *status, int32_t *counters, void *stream);
+
+/* Totals of the last kin_integrate_exprb call in the counters' order (0..6),
+ * failed states (7) and the largest step count (8); KIN_ERR_STATE_FAILED
+ * when a state failed. */
+int kin_exprb_get_stats(kin_exprb *x, int64_t *out);
+
+/* The matrix functions the Krylov products use, as a unit-level entry for
+ * testing: out[i*p + k-1] = (phi_k(tau H) e1)_i for k = 1..p, i < m, H dev
+ * [m*m] row-major, out dev [m*p]; 1 <= m <= ns, 1 <= p <= 5.  Runs on one
+ * warp in the first workspace slot (no integration may be in flight).
+ * KIN_ERR_INVALID_ARG outside those ranges; NaN when the Pade denominator is
+ * singular or tau H is not finite. */
+int kin_exprb_phi(kin_exprb *x, const double *H, int32_t m, int32_t p, double tau, double *out,
+                  void *stream);
+
+/* The right-hand side and analytical Jacobian exprb43 evaluates (those of the
+ * state-per-warp kernels), as a unit-level entry for testing: y dev [N][n]
+ * (N = ns, y = [T, Y_0..Y_{ns-2}]), P dev [n]; f dev [N][n] from the
+ * evaluation that assembles J, f_rates dev [N][n] from the rate-only
+ * evaluation, J dev [N*N][n] with entry (r, c) at J[(r*N + c)*n + i].  No
+ * integration may be in flight on x. */
+int kin_exprb_chem(kin_exprb *x, const double *y, const double *P, int64_t n, double *f,
+                   double *f_rates, double *J, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Step/guess predictor (the learned part; the paper has no counterpart).
  * An MLP x (din) -> 3 x [Linear(width) -> SiLU] -> Linear(dout) trained on
  * first steps the integrator itself produced, predicting the first internal

@@ -18,12 +18,18 @@ silent):
   J_n is the analytical Jacobian at u_n, evaluated once per new point (kept
   across rejected attempts);
 - each of the three vectors F(u_n), D2, D3 spans its own Krylov space
-  (Arnoldi, modified Gram-Schmidt) and phi_k(tau J) v is taken as
-  beta V_m phi_k(tau H_m) e1 (Sec. 2.1, after Saad);
+  (Arnoldi, modified Gram-Schmidt), built in the inner product of the step's
+  error weights D = diag(atol + rtol |u_n|): on D^-1 J D from D^-1 v, so
+  that phi_k(tau J) v = D beta V_m phi_k(tau H_m) e1 (Sec. 2.1, after Saad).
+  In mass fractions and kelvin J is badly scaled (the temperature row is
+  ~1e17 s^-1 on CH4), and the Euclidean Hessenberg's norm then asks for
+  40 squarings of its exponential; in the weighted product it reflects the
+  chemical time scales;
 - the dimension m grows until Saad's leading error term of every product the
   scheme takes from that space, h beta (h h_{m+1,m}) c_k |e_m^T phi_{k+1}(h
   H_m) e1| ||v_{m+1}||_w (c_k the product's coefficient, ||.||_w the RMS norm
-  in the step's error weights), is at most kappa; or until the space is
+  in the error weights, 1/sqrt(N) for the unit basis vector), is at most
+  kappa (a non-finite estimate is not below it); or until the space is
   exhausted (h_{m+1,m} <= 1e-13 ||J v_m||, "happy breakdown") or m = N;
 - phi_1 .. phi_p(A) e1 from the exponential of the augmented matrix
   [[A, e1, 0], [0, 0, I], [0, 0, 0]] (scipy.linalg.expm, a library primitive);
@@ -67,8 +73,12 @@ def wrms(v, scal):
 
 
 def arnoldi(J, v, h, products, scal, kappa):
-    """Arnoldi on J from v with the stopping rule above.  Returns (beta, V
-    [N, m], H [m, m], m); beta = 0 and m = 0 for v = 0."""
+    """Arnoldi on J from v with the stopping rule above, in the inner product
+    the error weights define: the basis is that of D^-1 J D from D^-1 v,
+    D = diag(scal).  Returns (beta, V [N, m], H [m, m], m) of the scaled
+    space; beta = 0 and m = 0 for v = 0."""
+    J = J * scal[None, :] / scal[:, None]
+    v = v / scal
     N = v.shape[0]
     beta = float(np.linalg.norm(v))
     if beta == 0.0:
@@ -89,19 +99,22 @@ def arnoldi(J, v, h, products, scal, kappa):
             return beta, V[:, :m], H[:m, :m], m
         V[:, j + 1] = w / H[j + 1, j]
         ph = phi_vectors(h * H[:m, :m], kmax + 1)
-        lead = max(c * abs(ph[k][m - 1]) for k, c in products)  # ph[k] is phi_{k+1}
-        est = h * beta * (h * H[j + 1, j]) * lead * wrms(V[:, j + 1], scal)
+        vals = [c * abs(ph[k][m - 1]) for k, c in products]  # ph[k] is phi_{k+1}
+        lead = float("nan") if any(np.isnan(vals)) else max(vals)  # no estimate: keep growing
+        # v_{m+1} has unit 2-norm in the scaled space: its weighted RMS is 1/sqrt(N)
+        est = h * beta * (h * H[j + 1, j]) * lead / np.sqrt(N)
         if est <= kappa:
             return beta, V[:, :m], H[:m, :m], m
     raise AssertionError("unreachable")
 
 
-def _products(beta, V, H, tau, ks):
-    """{k: phi_k(tau J) v} for the Krylov space (beta, V, H)."""
+def _products(beta, V, H, tau, ks, scal):
+    """{k: phi_k(tau J) v} for the (scaled) Krylov space (beta, V, H):
+    D beta V phi_k(tau H) e1."""
     if beta == 0.0:
         return {k: np.zeros(V.shape[0]) for k in ks}
     ph = phi_vectors(tau * H, max(ks))
-    return {k: beta * (V @ ph[k - 1]) for k in ks}
+    return {k: scal * (beta * (V @ ph[k - 1])) for k in ks}
 
 
 def step(f, J, u, fu, h, scal, kappa):
@@ -109,22 +122,22 @@ def step(f, J, u, fu, h, scal, kappa):
     Krylov dimensions, right-hand sides used); u_new None if a stage is not
     finite."""
     b1, V1, H1, m1 = arnoldi(J, fu, h, PRODUCTS_F, scal, kappa)
-    half = _products(b1, V1, H1, 0.5 * h, (1,))[1]
-    full = _products(b1, V1, H1, h, (1,))[1]
+    half = _products(b1, V1, H1, 0.5 * h, (1,), scal)[1]
+    full = _products(b1, V1, H1, h, (1,), scal)[1]
     U2 = u + 0.5 * h * half
     F2 = f(U2)
     if not np.all(np.isfinite(F2)):
         return None, None, (m1, 0, 0), 1
     D2 = F2 - fu - J @ (U2 - u)
     b2, V2, H2, m2 = arnoldi(J, D2, h, PRODUCTS_D2, scal, kappa)
-    q = _products(b2, V2, H2, h, (1, 3, 4))
+    q = _products(b2, V2, H2, h, (1, 3, 4), scal)
     U3 = u + h * full + h * q[1]
     F3 = f(U3)
     if not np.all(np.isfinite(F3)):
         return None, None, (m1, m2, 0), 2
     D3 = F3 - fu - J @ (U3 - u)
     b3, V3, H3, m3 = arnoldi(J, D3, h, PRODUCTS_D3, scal, kappa)
-    r = _products(b3, V3, H3, h, (3, 4))
+    r = _products(b3, V3, H3, h, (3, 4), scal)
     base = u + h * full
     unew = base + h * (16.0 * q[3] - 48.0 * q[4]) + h * (-2.0 * r[3] + 12.0 * r[4])
     uhat = base + h * (16.0 * q[3]) + h * (-2.0 * r[3])

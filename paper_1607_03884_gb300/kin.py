@@ -33,7 +33,8 @@ EXPORTS = ("kin_options_default", "kin_mech_create", "kin_destroy", "kin_integra
            "kin_mlp_train_step", "kin_moments", "kin_mlp_features", "kin_mlp_targets",
            "kin_mlp_predict", "kin_autotune", "kin_order_states", "kin_mlp_train_step_rows",
            "kin_resolve_options", "kin_conc_analyse", "kin_conc_create", "kin_conc_destroy",
-           "kin_integrate_conc", "kin_conc_get_stats")
+           "kin_integrate_conc", "kin_conc_get_stats", "kin_exprb_create", "kin_exprb_destroy",
+           "kin_integrate_exprb", "kin_exprb_get_stats", "kin_exprb_phi", "kin_exprb_chem")
 
 
 class KinError(RuntimeError):
@@ -112,6 +113,13 @@ def lib():
             L.kin_conc_destroy.argtypes = [vp]
             L.kin_integrate_conc.argtypes = [vp, vp, vp, vp, i64, d, d, d, vp, vp, vp, vp]
             L.kin_conc_get_stats.argtypes = [vp, vp]
+            L.kin_exprb_create.argtypes = [vp, C.POINTER(vp)]
+            L.kin_exprb_destroy.argtypes = [vp]
+            L.kin_integrate_exprb.argtypes = [vp, vp, vp, vp, i64, d, d, d, d, vp, i32, vp, vp,
+                                              vp]
+            L.kin_exprb_get_stats.argtypes = [vp, vp]
+            L.kin_exprb_phi.argtypes = [vp, vp, i32, i32, d, vp, vp]
+            L.kin_exprb_chem.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
             L.kin_status_string.argtypes = [C.c_int]
             L.kin_status_string.restype = C.c_char_p
             _lib = L
@@ -419,6 +427,69 @@ class ConcMechanism:
         if rc not in (KIN_OK, KIN_ERR_STATE_FAILED):
             _check(rc, "kin_conc_get_stats")
         keys = list(COUNTER_NAMES[:7]) + ["failed", "max_steps_state"]
+        return dict(zip(keys, out.tolist()))
+
+
+class ExpRosenbrock:
+    """exprb43 with Krylov phi-function products for a mechanism on the
+    current CUDA device (kin_exprb_create)."""
+
+    def __init__(self, mech):
+        self.ns, self.nr = int(mech.ns), int(mech.nr)
+        d, keep = mech_desc(mech)
+        h = C.c_void_p()
+        _check(lib().kin_exprb_create(C.byref(d), C.byref(h)), "kin_exprb_create")
+        del keep
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.kin_exprb_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate(self, Y, T, P, dt, rtol=1e-6, atol=1e-10, *, kappa=0.1, h0=None,
+                  max_steps=100000, status=None, counters=None, stream=None):
+        """Advance device tensors Y [ns, n], T [n] in place over dt (kin_integrate_exprb)."""
+        n = int(T.shape[0])
+        _check(lib().kin_integrate_exprb(self.handle, _ptr(Y), _ptr(T), _ptr(P), n, float(dt),
+                                         float(rtol), float(atol), float(kappa), _ptr(h0),
+                                         int(max_steps), _ptr(status), _ptr(counters),
+                                         _stream(stream)), "kin_integrate_exprb")
+
+    def phi(self, H, p, tau, out, stream=None):
+        """phi_1..phi_p (tau H) e1 of a device matrix H [m, m] into out [m, p]
+        (kin_exprb_phi)."""
+        m = int(H.shape[0])
+        _check(lib().kin_exprb_phi(self.handle, _ptr(H), m, int(p), float(tau), _ptr(out),
+                                   _stream(stream)), "kin_exprb_phi")
+
+    def chem(self, y, P, f, f_rates, J, stream=None):
+        """Right-hand sides and Jacobians of the state-per-warp kernels
+        (kin_exprb_chem): y [N, n], f and f_rates [N, n], J [N*N, n]."""
+        n = int(P.shape[0])
+        _check(lib().kin_exprb_chem(self.handle, _ptr(y), _ptr(P), n, _ptr(f), _ptr(f_rates),
+                                    _ptr(J), _stream(stream)), "kin_exprb_chem")
+
+    def stats(self):
+        """Totals of the last integration (kin_exprb_get_stats)."""
+        out = np.zeros(9, dtype=np.int64)
+        rc = lib().kin_exprb_get_stats(self.handle, out.ctypes.data)
+        if rc not in (KIN_OK, KIN_ERR_STATE_FAILED):
+            _check(rc, "kin_exprb_get_stats")
+        keys = ["nstep", "naccpt", "nrejct", "nfcn", "njac", "krylov_spaces", "krylov_dim",
+                "failed", "max_steps_state"]
         return dict(zip(keys, out.tolist()))
 
 

@@ -55,14 +55,21 @@ def test_arnoldi_relation_and_exhaustion():
     np.testing.assert_allclose(V.T @ V, np.eye(N), atol=1e-12)
     np.testing.assert_allclose(J @ V, V @ H, atol=1e-11)              # exhausted: exact
     np.testing.assert_allclose(beta * V[:, 0], v, rtol=1e-14)
+    # with error weights the space is that of D^-1 J D from D^-1 v
+    sc = rng.uniform(0.1, 10.0, size=N)
+    beta, V, H, m = X.arnoldi(J, v, 1e-3, X.PRODUCTS_F, sc, 0.0)
+    Js = J * sc[None, :] / sc[:, None]
+    np.testing.assert_allclose(V.T @ V, np.eye(N), atol=1e-12)
+    np.testing.assert_allclose(Js @ V, V @ H, atol=1e-10)
+    np.testing.assert_allclose(beta * V[:, 0] * sc, v, rtol=1e-13)
     # a looser kappa never takes more dimensions
-    ms = [X.arnoldi(J, v, 1e-3, X.PRODUCTS_F, scal, k)[3] for k in (0.0, 1e-12, 1e-6, 1e-2)]
+    ms = [X.arnoldi(J, v, 1e-3, X.PRODUCTS_F, scal, k)[3] for k in (0.0, 1e-12, 1e-6, 1e-2, 1.0)]
     assert all(a >= b for a, b in zip(ms, ms[1:])) and ms[-1] < N
 
 
 def test_linear_problems_are_integrated_exactly():
     """y' = A y + b: g = b is constant, D2 = D3 = 0 and one step is the exact
-    flow e^{hA} y + h phi1(hA) b (exact Krylov space)."""
+    flow e^{hA} y + h phi1(hA) b (exact Krylov space, weighted)."""
     rng = np.random.default_rng(4)
     N = 6
     Q, _ = np.linalg.qr(rng.normal(size=(N, N)))
