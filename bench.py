@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--config3-only", default=None, choices=["massfrac", "conc"],
                    help="time only configuration 3 in the given form (states = --n, default "
                         "2^18)")
+    p.add_argument("--exprb-only", action="store_true",
+                   help="time only exprb43 on the first --n states (default 2^16) at --dt")
     p.add_argument("--mlp-only", action="store_true",
                    help="time only the predictor's training step (rows = --n, default 2^16)")
     p.add_argument("--cpu-sample", type=int, default=2048)
@@ -627,6 +629,11 @@ def main():
     if args.config3_only:   # configuration 3 alone, in one form (for profiling its kernel)
         import torch
         print(json.dumps(config3_leg(torch.cuda.current_stream(), args.config3_only, args.n)))
+        return
+    if args.exprb_only:   # exprb43 alone (for profiling its kernel)
+        import torch
+        print(json.dumps(exprb_leg(torch.cuda.current_stream(), n=args.n or (1 << 16),
+                                   dt=args.dt)))
         return
     if args.mlp_only:   # the predictor's training step alone (for profiling its GEMMs)
         import torch
