@@ -16,6 +16,8 @@
 // Features for the integrator: log T, log P, log dt, log10(max(Y_k, 1e-12))
 // (all species), standardised with caller-given moments; outputs: log h0 and
 // the 3 N stage increments, de-standardised.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -53,8 +55,14 @@ __device__ __forceinline__ float silu_grad(float a) {
 // completion is signalled on an mbarrier before the slice is overwritten.
 // The epilogue reads the accumulator back with tcgen05.ld (warp w owns TMEM
 // lanes 32w..32w+31, the tile's rows) and writes or adds C.  Every wait is
-// bounded: on expiry the kernel sets *err, waits (bounded) for its MMAs,
-// frees its TMEM and returns.
+// bounded: on expiry the kernel sets *err, waits (bounded) for its MMAs and
+// loads, frees its TMEM and returns.
+// A K-contiguous operand with 16-byte rows (the forward pass and the input
+// gradients) is loaded by the tensor memory accelerator instead: one thread
+// issues eight cp.async.bulk.tensor boxes of 8 K x 128 rows per slice, each
+// landing as 16 core matrices in a row (core (g, c) at c * 2048 + g * 128
+// bytes), completion counted in bytes on a second mbarrier; the TMA fills
+// rows and K past the matrix with zeros.
 // ---------------------------------------------------------------------------
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
 constexpr int TC_THREADS = 128;
@@ -123,19 +131,25 @@ __device__ __forceinline__ void tc_stage_row(unsigned char *dst, const __nv_bflo
 
 // Split K: CTA z sums K in [z kchunk, min(K, (z + 1) kchunk)) and writes its
 // partial tile to C + z cz (the caller reduces the partials).
+// tma: bit 0 loads A, bit 1 loads B through the tensor maps (rows x K, K
+// innermost, boxes of 8 x 128); the split-K chunks are multiples of the slice
 __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
                                                        const __nv_bfloat16 *A, int64_t sam,
                                                        int64_t sak, const __nv_bfloat16 *B,
                                                        int64_t sbk, int64_t sbn, float *C,
                                                        int64_t ldc, int accumulate, int *err,
-                                                       int kchunk, int64_t cz) {
+                                                       int kchunk, int64_t cz,
+                                                       const __grid_constant__ CUtensorMap tmA,
+                                                       const __grid_constant__ CUtensorMap tmB,
+                                                       int tma) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ __align__(8) unsigned long long mbar, mfull;
   __shared__ uint32_t tmem_base;
   unsigned char *sA = tc_smem, *sB = tc_smem + TC_BM * TC_BK * 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-  const uint32_t mb = smem_u32(&mbar);
+  const uint32_t mb = smem_u32(&mbar), mf = smem_u32(&mfull);
+  const bool ta = (tma & 1) != 0, tb = (tma & 2) != 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base)),
@@ -145,6 +159,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mf) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -158,13 +173,35 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
   const bool a_vec = a_k1 && sam % 8 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
   const bool b_vec = b_k1 && sbn % 8 == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
   const bool a_kfast = sak <= sam, b_kfast = sbk <= sbn;
-  uint32_t phase = 0;
-  bool ok = true;
+  uint32_t phase = 0, fphase = 0;
+  bool ok = true, tma_pending = false;
   const int nk = (ke - kb + TC_BK - 1) / TC_BK;
   for (int kt = 0; kt < nk && ok; ++kt) {
     const int k0 = kb + kt * TC_BK;
-    // stage the slices (zero outside the matrices and the K range)
-    if (a_k1) {
+    if ((ta || tb) && tid == 0) {  // x = k0 + 8 j: a multiple of 8 elements (16 bytes)
+      const uint32_t bytes = (ta ? TC_BM * TC_BK * 2u : 0u) + (tb ? TC_BN * TC_BK * 2u : 0u);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mf), "r"(bytes)
+                   : "memory");
+#pragma unroll
+      for (int j = 0; j < TC_BK / 8; ++j) {
+        if (ta)
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(sA) + (uint32_t)(j * TC_BM * 16)),
+              "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(k0 + 8 * j), "r"(m0), "r"(mf)
+              : "memory");
+        if (tb)
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(sB) + (uint32_t)(j * TC_BN * 16)),
+              "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(k0 + 8 * j), "r"(n0), "r"(mf)
+              : "memory");
+      }
+    }
+    tma_pending = ta || tb;
+    // stage the other slices (zero outside the matrices and the K range)
+    if (ta) {
+    } else if (a_k1) {
       for (int e = tid; e < TC_BM * (TC_BK / 8); e += TC_THREADS) {
         const int r = e >> 3, kc = (e & 7) * 8, gm = m0 + r;
         tc_stage_row(sA + tc_off(r, kc), A + (int64_t)(gm < M ? gm : 0) * sam, 1, a_vec,
@@ -179,7 +216,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
         *reinterpret_cast<__nv_bfloat16 *>(sA + tc_off(r, k)) = v;
       }
     }
-    if (b_k1) {
+    if (tb) {
+    } else if (b_k1) {
       for (int e = tid; e < TC_BN * (TC_BK / 8); e += TC_THREADS) {
         const int c = e >> 3, kc = (e & 7) * 8, gn = n0 + c;
         tc_stage_row(sB + tc_off(c, kc), B + (int64_t)(gn < N ? gn : 0) * sbn, 1, b_vec,
@@ -197,14 +235,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
     // make the generic-proxy writes visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (ta || tb) {  // the TMA boxes have landed
+      ok = __syncthreads_and(tc_wait(mf, fphase)) != 0;
+      fphase ^= 1u;
+      tma_pending = !ok;
+      if (!ok) break;
+    }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t idesc = tc_idesc(TC_BM, TC_BN);
 #pragma unroll
       for (int s = 0; s < TC_BK / 16; ++s) {
         // k16 step s covers K cores 2s and 2s + 1
-        const uint64_t da = tc_desc(smem_u32(sA) + 256u * s, 128u, (TC_BK / 8) * 128u);
-        const uint64_t db = tc_desc(smem_u32(sB) + 256u * s, 128u, (TC_BK / 8) * 128u);
+        // K cores 128 B apart, 8-row groups 1024 B (threads' layout); or K
+        // cores 2048 B apart, row groups 128 B (the TMA boxes)
+        const uint64_t da = ta ? tc_desc(smem_u32(sA) + 4096u * s, 2048u, 128u)
+                               : tc_desc(smem_u32(sA) + 256u * s, 128u, (TC_BK / 8) * 128u);
+        const uint64_t db = tb ? tc_desc(smem_u32(sB) + 4096u * s, 2048u, 128u)
+                               : tc_desc(smem_u32(sB) + 256u * s, 128u, (TC_BK / 8) * 128u);
         const uint32_t acc = (kt > 0 || s > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -249,7 +297,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int K,
     }
   } else {
     if (tid == 0) atomicOr(err, 1);
-    (void)tc_wait(mb, phase ^ 1u);  // the last commit, if it is still pending
+    if (tma_pending) (void)tc_wait(mf, fphase);  // boxes still landing
+    else (void)tc_wait(mb, phase ^ 1u);          // the last commit, if it is still pending
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -516,10 +565,55 @@ static int mlp_reserve(kin_mlp *n, int64_t rows) {
   return KIN_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    (void)cudaGetLastError();
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// tensor map of a rows x cols BF16 matrix with row stride ld (elements),
+// boxes of 8 columns x 128 rows, zero fill outside; false when the layout
+// does not allow the TMA (16-byte base and rows)
+static bool make_tmap(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld) {
+  std::memset(m, 0, sizeof *m);
+  auto enc = tmap_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || ld < cols ||
+      rows < 1 || cols < 1)
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {8, 128}, es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// TMA operand loads (1) or the threads' copies only (0): a build-time knob
+#ifndef KIN_MLP_TMA
+#define KIN_MLP_TMA 1
+#endif
+
 static void gemm(const kin_mlp *n, cudaStream_t st, int M, int N, int K, bool bf, const void *A,
                  int64_t sam, int64_t sak, const void *B, int64_t sbk, int64_t sbn, float *C,
                  int64_t ldc, int acc) {
   if (bf) {
+    CUtensorMap tmA, tmB;
+    int tma = 0;
+    if (KIN_MLP_TMA && sak == 1 && make_tmap(&tmA, A, M, K, sam)) tma |= 1;
+    if (KIN_MLP_TMA && sbk == 1 && make_tmap(&tmB, B, N, K, sbn)) tma |= 2;
+    if (!(tma & 1)) std::memset(&tmA, 0, sizeof tmA);
+    if (!(tma & 2)) std::memset(&tmB, 0, sizeof tmB);
     dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN, 1);
     // few output tiles and a long K (the weight gradients: K = batch rows):
     // split K over up to 2 x 152 CTAs, partial tiles reduced in fixed order
@@ -535,12 +629,14 @@ static void gemm(const kin_mlp *n, cudaStream_t st, int M, int N, int K, bool bf
       grid.z = S;
       k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(M, N, K, (const __nv_bfloat16 *)A, sam, sak,
                                                    (const __nv_bfloat16 *)B, sbk, sbn, n->ws, N,
-                                                   0, n->err, kchunk, (int64_t)M * N);
+                                                   0, n->err, kchunk, (int64_t)M * N, tmA, tmB,
+                                                   tma);
       k_splitk_reduce<<<blocks((int64_t)M * N), 256, 0, st>>>(M, N, S, n->ws, C, ldc, acc);
     } else {
       k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(M, N, K, (const __nv_bfloat16 *)A, sam, sak,
                                                    (const __nv_bfloat16 *)B, sbk, sbn, C, ldc,
-                                                   acc, n->err, (int)kt * TC_BK, 0);
+                                                   acc, n->err, (int)kt * TC_BK, 0, tmA, tmB,
+                                                   tma);
     }
   } else {
     k_gemm_f32<<<blocks((int64_t)M * N), 256, 0, st>>>(M, N, K, (const float *)A, sam, sak,
