@@ -115,7 +115,8 @@ __device__ __noinline__ int conc_chem(const MechView &m, const ConcView &cv, con
       const int meta = m.meta[i];
       const int *sl = m.slot + 6 * i;
       const int nre = meta_nreac(meta), npr = meta_nprod(meta), type = meta_type(meta);
-      const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
+      const double lnkf = m.lnA[i] + m.b[i] * logT - m.Th[i] * invT;
+      const double kf = kexp(lnkf, m.etab);
       double lnKc = m.dnu[i] * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
       for (int s = 0; s < nre; ++s) {
         lnKc -= b.g[sl[s]];
@@ -138,7 +139,7 @@ __device__ __noinline__ int conc_chem(const MechView &m, const ConcView &cv, con
           dphi_dM = 1.0;
         } else {
           const TroeOut t = troe_factor<true>(m.troe + NTROE * meta_troe(meta), T, logT, invT,
-                                              kf, dlnkf, M, m.etab);
+                                              lnkf, dlnkf, M, m.etab);
           phi = t.P;
           dphi_dT = t.P * t.dlnP_dT;
           dphi_dM = t.P * t.dlnP_dM;

@@ -157,7 +157,9 @@ __device__ __forceinline__ double kexp(double x, const double *tab) {
 
 // ---------------------------------------------------------------------------
 // Troe falloff factor Pfac = Pr/(1+Pr) F, Pr = k0 [M] / k_inf, with its
-// logarithmic derivatives in T (at fixed [M]) and in [M].
+// logarithmic derivatives in T (at fixed [M]) and in [M].  lnkinf is the
+// high-pressure rate's Arrhenius exponent (ln k_inf), so ln Pr is formed from
+// the two exponents and ln [M] without dividing the rate constants.
 // ---------------------------------------------------------------------------
 struct TroeOut {
   double P, dlnP_dT, dlnP_dM;
@@ -165,26 +167,27 @@ struct TroeOut {
 
 template <bool DERIV>
 __device__ __forceinline__ TroeOut troe_factor(const double *tp, double T, double logT,
-                                               double invT, double kinf, double dlnkinf,
+                                               double invT, double lnkinf, double dlnkinf,
                                                double M, const double *etab) {
   TroeOut o;
-  double k0 = kexp(tp[0] + tp[1] * logT - tp[2] * invT, etab);
   double a = tp[3];
   double e3 = kexp(-T * tp[4], etab), e1 = kexp(-T * tp[5], etab), e2 = kexp(-tp[6] * invT, etab);
   double Fc = (1.0 - a) * e3 + a * e1 + e2;
   double lFc = log10(Fc);
-  double Pr = k0 * M / kinf;
-  double L = log10(Pr);
+  const double lnPr = (tp[0] + tp[1] * logT - tp[2] * invT) - lnkinf + log(M);
+  const double Pr = kexp(lnPr, etab);
+  const double L = lnPr * (1.0 / LN10);  // log10 Pr
   double c = -0.4 - 0.67 * lFc, nn = 0.75 - 1.27 * lFc;
   const double d = 0.14;
   double u = L + c, v = nn - d * u;
-  double X = u / v;
-  double den = 1.0 + X * X;
-  double lF = lFc / den;
-  o.P = Pr / (1.0 + Pr) * kexp(lF * LN10, etab);
+  // log10 F = lFc / (1 + (u/v)^2) = lFc v^2 / (v^2 + u^2): one division
+  const double v2 = v * v;
+  o.P = Pr / (1.0 + Pr) * kexp(lFc * v2 / (v2 + u * u) * LN10, etab);
   o.dlnP_dT = 0.0;
   o.dlnP_dM = 0.0;
   if (DERIV) {
+    double X = u / v;
+    double den = 1.0 + X * X;
     double dFc = -(1.0 - a) * tp[4] * e3 - a * tp[5] * e1 + tp[6] * invT * invT * e2;
     double dX_dL = nn / (v * v);
     double dv = -1.27 + d * 0.67;
@@ -224,6 +227,31 @@ struct ChemScratch {
   double C[MAXN], g[MAXN], hs[MAXN], cpk[MAXN], wd[MAXN];
 };
 
+// One thread's vector in the block's shared memory, element k at p[k * stride]:
+// the threads of a block are interleaved, so a warp's accesses to the same k
+// are consecutive doubles (no bank conflicts).
+struct SmemVec {
+  double *p;
+  int stride;
+  __device__ __forceinline__ double &operator[](int k) const { return p[k * stride]; }
+};
+
+// The same scratch with the arrays the reaction loop gathers from and scatters
+// to (C, g, wdot) in shared memory, the others in the thread's own memory.
+template <int MAXN>
+struct ChemScratchS {
+  SmemVec C, g, wd;
+  double hs[MAXN], cpk[MAXN];
+  // three vectors of ns doubles per thread of the block, at base
+  __device__ __forceinline__ void bind(double *base, int ns) {
+    const int nt = blockDim.x, t = threadIdx.x;
+    C = SmemVec{base + t, nt};
+    g = SmemVec{base + ns * nt + t, nt};
+    wd = SmemVec{base + 2 * ns * nt + t, nt};
+  }
+  __host__ __device__ static size_t bytes(int ns, int nt) { return 3 * sizeof(double) * ns * nt; }
+};
+
 template <int MAXN, typename JT>
 struct JacScratch {
   JT A[MAXN], B[MAXN], Tc[MAXN], mj[MAXN], Cj[MAXN], rW[MAXN];
@@ -237,9 +265,9 @@ struct JacScratch {
 #endif
 constexpr int RHS_UNROLL = KIN_RHS_UNROLL;
 
-template <int MAXN, typename JT>
+template <int MAXN, typename JT, typename CS>
 __device__ __noinline__ int chem_eval(const MechView &m, double P, const double *y,
-                                      double *f, JT *J, bool wantJ, ChemScratch<MAXN> &w,
+                                      double *f, JT *J, bool wantJ, CS &w,
                                       JacScratch<MAXN, JT> &x) {
   const int ns = m.ns, in = ns - 1, N = ns;
   const double T = y[0];
@@ -257,19 +285,21 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
 #pragma unroll RHS_UNROLL
   for (int k = 0; k < ns; ++k) {
     const double Yk = (k < in) ? y[1 + k] : Yin;
-    w.C[k] = rho * Yk * m.invW[k];
-    const int r = range_of(m, k, T);
+    const double YW = Yk * m.invW[k];
+    w.C[k] = rho * YW;
+    // the range test on the bit patterns (both are positive): integer pipe
+    const int r = (__double_as_longlong(T) < __double_as_longlong(m.Tmid[k])) ? 0 : 1;
     const double *cc = m.cp + (2 * k + r) * NCP;
     const double cp = poly_cp(cc, T);
     const double h = poly_h(m.h + (2 * k + r) * NH, T, invT);
     w.g[k] = poly_g(m.gb + (2 * k + r) * NG, T, logT, invT);
     w.hs[k] = h;
-    w.cpk[k] = cp;
-    cpm += Yk * cp * m.invW[k];
+    cpm = fma(YW, cp, cpm);
     w.wd[k] = 0.0;
     if (wantJ) {
+      w.cpk[k] = cp;  // per-species cp only for the Jacobian's temperature terms
       x.dcp[k] = poly_dcp(cc, T);
-      dcpm += Yk * x.dcp[k] * m.invW[k];
+      dcpm = fma(YW, x.dcp[k], dcpm);
       x.A[k] = JT(0);
       x.B[k] = JT(0);
       x.Tc[k] = JT(0);
@@ -288,22 +318,25 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
     const int meta = m.meta[i];
     const int *sl = m.slot + 6 * i;
     const int nre = meta_nreac(meta), npr = meta_nprod(meta), type = meta_type(meta);
-    const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
-    double lnKc = m.dnu[i] * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
-    for (int s = 0; s < nre; ++s) {
+    const double lnkf = m.lnA[i] + m.b[i] * logT - m.Th[i] * invT;
+    const double kf = kexp(lnkf, m.etab);
+    // every reaction has a reactant and a product (checked when the mechanism
+    // is created): the first of each seeds the Gibbs sum and the products
+    double fwd = w.C[sl[0]], rev = w.C[sl[3]];
+    double lnKc = fma(m.dnu[i], lnPf, w.g[sl[3]] - w.g[sl[0]]);
+    for (int s = 1; s < nre; ++s) {
       lnKc -= w.g[sl[s]];
-      dH -= w.hs[sl[s]];
       fwd *= w.C[sl[s]];
     }
-    for (int s = 0; s < npr; ++s) {
+    for (int s = 1; s < npr; ++s) {
       lnKc += w.g[sl[3 + s]];
-      dH += w.hs[sl[3 + s]];
       rev *= w.C[sl[3 + s]];
     }
-    const double kr = kf * kexp(-lnKc, m.etab);
+    const double iKc = kexp(-lnKc, m.etab);  // 1 / Kc, so kr = kf / Kc
     double phi = 1.0, dphi_dT = 0.0, dphi_dM = 0.0, M = Ctot;
     const int e0 = m.eff0[i], ne = meta_neff(meta);
-    const double dlnkf = m.b[i] * invT + m.Th[i] * invT * invT;
+    // d ln kf / dT, needed only for the Jacobian
+    const double dlnkf = wantJ ? m.b[i] * invT + m.Th[i] * invT * invT : 0.0;
     if (type != 0) {
       for (int e = 0; e < ne; ++e) M += m.eff[e0 + e] * w.C[m.effsp[e0 + e]];
       if (type == 1) {
@@ -312,19 +345,23 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
       } else {
         // the derivatives only when the Jacobian is assembled
         const double *tp = m.troe + NTROE * meta_troe(meta);
-        TroeOut t = wantJ ? troe_factor<true>(tp, T, logT, invT, kf, dlnkf, M, m.etab)
-                          : troe_factor<false>(tp, T, logT, invT, kf, dlnkf, M, m.etab);
+        TroeOut t = wantJ ? troe_factor<true>(tp, T, logT, invT, lnkf, dlnkf, M, m.etab)
+                          : troe_factor<false>(tp, T, logT, invT, lnkf, dlnkf, M, m.etab);
         phi = t.P;
         dphi_dT = t.P * t.dlnP_dT;
         dphi_dM = t.P * t.dlnP_dM;
       }
     }
-    const double Rn = kf * fwd - kr * rev;
-    const double q = phi * Rn;
+    const double Rn = kf * fma(-iKc, rev, fwd);  // kf prod C' - kr prod C''
+    const double q = (type != 0) ? phi * Rn : Rn;
     for (int s = 0; s < nre; ++s) w.wd[sl[s]] -= q;
     for (int s = 0; s < npr; ++s) w.wd[sl[3 + s]] += q;
     if (wantJ) {
+      const double kr = kf * iKc;
       // d ln Kc / dT = sum nu (h/RT) / T - (sum nu) / T
+      double dH = 0.0;
+      for (int s = 0; s < nre; ++s) dH -= w.hs[sl[s]];
+      for (int s = 0; s < npr; ++s) dH += w.hs[sl[3 + s]];
       const double dlnkr = dlnkf - (dH - m.dnu[i]) * invT;
       const double u = Rn * dphi_dM;
       const double sig_p = phi * (nre * kf * fwd - npr * kr * rev) + u * (M - Ctot);
@@ -364,43 +401,48 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
       }
     }
   }
-  double Hw = 0.0, CPw = 0.0;
-  for (int k = 0; k < in; ++k) {
-    Hw += w.hs[k] * w.wd[k];
-    CPw += w.cpk[k] * w.wd[k];
-  }
+  double Hw = 0.0;
+  for (int k = 0; k < in; ++k) Hw += w.hs[k] * w.wd[k];
   // f_T = -sum_k H_k wdot_k / (rho cp),  H_k = (h/RT) Ru T, cp = Ru cpm
   f[0] = -(Hw * T) / (rho * cpm);
-  bool ok = isfinite(f[0]);
+  // finiteness on the exponent bits (integer pipe): all ones = inf or NaN
+  int nonfinite = (__double2hiint(f[0]) & 0x7ff00000) == 0x7ff00000;
   const double irho = 1.0 / rho;
   for (int k = 0; k < in; ++k) {
     f[1 + k] = m.W[k] * w.wd[k] * irho;
-    ok &= isfinite(f[1 + k]);
+    nonfinite |= (__double2hiint(f[1 + k]) & 0x7ff00000) == 0x7ff00000;
   }
-  if (!wantJ) return ok ? 0 : 4;
+  if (!wantJ) return nonfinite ? 4 : 0;
+  bool ok = !nonfinite;
+  double CPw = 0.0;
+  for (int k = 0; k < in; ++k) CPw += w.cpk[k] * w.wd[k];
   // rank-one and inert terms, then the temperature column of dwdot/dy
-  const JT rWin = x.rW[in], iS = JT(1.0 / S);
+  const double iSd = 1.0 / S;
+  const JT rWin = x.rW[in], iS = JT(iSd);
   for (int k = 0; k < in; ++k) {
     JT *Jr = J + (1 + k) * N;
     Jr[0] = x.Tc[k];
     const JT a = rWin * x.A[k], b = iS * x.B[k];
     for (int j = 0; j < in; ++j) Jr[1 + j] -= a + x.mj[j] * b;
   }
-  // T row from the dwdot/dy rows (before they are scaled)
+  // T row from the dwdot/dy rows (before they are scaled); h/RT in the
+  // matrix type once per species (the Cj scratch is free by now)
+  for (int k = 0; k < in; ++k) x.Cj[k] = JT(w.hs[k]);
   const double HwJ = Hw * RU * T;      // sum H_k wdot_k
   const double CPwJ = CPw * RU;        // sum Cp_k wdot_k
   const double rcp = rho * cpm * RU;
   const double cpin = w.cpk[in] * m.invW[in];
   const JT hfac = JT(RU * T / rcp);    // dHw/dy enters as -RU T sum h_k J_kc / rcp
   const JT g2 = JT(HwJ / (rcp * rcp));
+  const double rhoS = rho * iSd;
   for (int c = 0; c < N; ++c) {
     JT dh = JT(0);
-    for (int k = 0; k < in; ++k) dh += JT(w.hs[k]) * J[(1 + k) * N + c];
+    for (int k = 0; k < in; ++k) dh += x.Cj[k] * J[(1 + k) * N + c];
     double drcp;
     if (c == 0) {
       drcp = cpm * RU * (-rho * invT) + rho * dcpm * RU;
     } else {
-      drcp = cpm * RU * (-rho * (m.invW[c - 1] - m.invW[in]) / S) +
+      drcp = cpm * RU * (-rhoS * (m.invW[c - 1] - m.invW[in])) +
              rho * (w.cpk[c - 1] * m.invW[c - 1] - cpin) * RU;
     }
     const JT extra = (c == 0) ? JT(-CPwJ / rcp) : JT(0);
@@ -410,17 +452,18 @@ __device__ __noinline__ int chem_eval(const MechView &m, double P, const double 
     JT *Jr = J + (1 + k) * N;
     const JT a = JT(m.W[k] * irho), bb = JT(m.W[k] * w.wd[k] * irho * irho);
     Jr[0] = a * Jr[0] + bb * JT(rho * invT);
-    const JT bS = bb * JT(rho / S);
+    const JT bS = bb * JT(rhoS);
     for (int j = 0; j < in; ++j) Jr[1 + j] = a * Jr[1 + j] + bS * x.mj[j];
   }
-  for (int q = 0; q < N * N; ++q) ok &= isfinite(double(J[q]));
+  // in the matrix type itself: no widening conversion per entry
+  for (int q = 0; q < N * N; ++q) ok &= isfinite(J[q]);
   return ok ? 0 : 4;
 }
 
 // f only (the Jacobian scratch is not touched when wantJ is false)
-template <int MAXN, typename JT>
+template <int MAXN, typename JT, typename CS>
 __device__ __forceinline__ int rhs(const MechView &m, double P, const double *y, double *f,
-                                   ChemScratch<MAXN> &w, JacScratch<MAXN, JT> &x) {
+                                   CS &w, JacScratch<MAXN, JT> &x) {
   return chem_eval<MAXN, JT>(m, P, y, f, (JT *)nullptr, false, w, x);
 }
 

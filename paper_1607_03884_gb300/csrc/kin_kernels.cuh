@@ -117,6 +117,36 @@ __device__ void store_state(const Work<MAXN, LT> &w, const StepState &s, const K
 #define KIN_THREAD_VIEW(a, smem) make_view((a).L, (a).tab, (a).itab)
 #endif
 
+// Dynamic shared memory of a thread-layout block: the staged tables (if any),
+// then the right-hand side's shared scratch (if any), 8-byte aligned.
+__host__ __device__ inline size_t thread_tables_bytes(const MechLayout &L) {
+#ifdef KIN_THREAD_TABLES_SMEM
+  return (smem_bytes(L) + 7) / 8 * 8;
+#else
+  (void)L;
+  return 0;
+#endif
+}
+template <int MAXN>
+__host__ __device__ inline size_t thread_smem_bytes(const MechLayout &L, int block) {
+#ifdef KIN_THREAD_SCRATCH_SMEM
+  return thread_tables_bytes(L) + ChemScratchS<MAXN>::bytes(L.ns, block);
+#else
+  (void)block;
+  return thread_tables_bytes(L);
+#endif
+}
+template <int MAXN, typename LT>
+__device__ __forceinline__ void bind_scratch(Work<MAXN, LT> &w, const KernelArgs &a, double *smem) {
+#ifdef KIN_THREAD_SCRATCH_SMEM
+  w.cs.bind(smem + thread_tables_bytes(a.L) / 8, a.L.ns);
+#else
+  (void)w;
+  (void)a;
+  (void)smem;
+#endif
+}
+
 template <int MAXN, typename LT, bool FDJ>
 __global__ void KIN_THREAD_BOUNDS k_integrate_plain(KernelArgs a) {
   extern __shared__ double smem[];
@@ -126,6 +156,7 @@ __global__ void KIN_THREAD_BOUNDS k_integrate_plain(KernelArgs a) {
   const int64_t i = state_of(a, slot);
   if (i < 0) return;
   Work<MAXN, LT> w;
+  bind_scratch(w, a, smem);
   StepState s;
   const int N = m.ns;
   load_state(w, a, N, i);
@@ -143,6 +174,7 @@ __global__ void KIN_THREAD_BOUNDS k_integrate_queue(KernelArgs a) {
   const int lane = threadIdx.x & 31;
   unsigned long long *queue = a.totals + 9;
   Work<MAXN, LT> w;
+  bind_scratch(w, a, smem);
   StepState s;
   int64_t idx = -1;
   double P = 0.0;
@@ -312,13 +344,9 @@ int launch_t(const KernelArgs &a, const kin_options &o, cudaStream_t st, int sms
       return KIN_ERR_UNSUPPORTED;
     }
   }
-#ifdef KIN_THREAD_TABLES_SMEM
-  const size_t sm = smem_bytes(a.L);
-#else
-  const size_t sm = 0;
-#endif
   const int block = o.block > 0 ? o.block : 64;
   if (block > 64 || block % 32) return KIN_ERR_INVALID_ARG;
+  const size_t sm = thread_smem_bytes<MAXN>(a.L, block);
   const int carve = KIN_THREAD_CARVEOUT;  // percent of the unified L1 given to shared memory
   if (o.layout == KIN_LAYOUT_PLAIN) {
     auto kern = k_integrate_plain<MAXN, LT, FDJ>;

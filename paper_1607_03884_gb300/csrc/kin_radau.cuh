@@ -54,6 +54,17 @@ struct RadauParams {
   double hfixed;       // > 0: constant steps, all accepted, a fresh J each step
 };
 
+// Where the thread layouts keep the right-hand side's gathered arrays: in the
+// thread's own (local) memory, or in shared memory (a build-time choice,
+// -DKIN_THREAD_SCRATCH_SMEM; the launcher then sizes the block's shared memory).
+#ifdef KIN_THREAD_SCRATCH_SMEM
+template <int MAXN>
+using WorkChem = ChemScratchS<MAXN>;
+#else
+template <int MAXN>
+using WorkChem = ChemScratch<MAXN>;
+#endif
+
 template <int MAXN, typename LT>
 struct Work {
   double y[MAXN], f0[MAXN], scal[MAXN], isc[MAXN];  // isc = 1 / scal
@@ -63,7 +74,7 @@ struct Work {
   LT J[MAXN * MAXN];  // the Jacobian is stored (and assembled) in the matrix type
   LT E1[MAXN * MAXN], E2r[MAXN * MAXN], E2i[MAXN * MAXN];
   int ip1[MAXN], ip2[MAXN];
-  ChemScratch<MAXN> cs;
+  WorkChem<MAXN> cs;
   JacScratch<MAXN, LT> js;
 };
 

@@ -228,7 +228,8 @@ __device__ __forceinline__ double falloff_rate(const MechView &m, const double *
   const int meta = m.meta[i];
   const int *sl = m.slot + 6 * i;
   const int nre = meta_nreac(meta), npr = meta_nprod(meta);
-  const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
+  const double lnkf = m.lnA[i] + m.b[i] * logT - m.Th[i] * invT;
+  const double kf = kexp(lnkf, m.etab);
   double lnKc = m.dnu[i] * lnPf, fwd = 1.0, rev = 1.0;
   for (int s = 0; s < nre; ++s) {
     lnKc -= g[sl[s]];
@@ -245,7 +246,7 @@ __device__ __forceinline__ double falloff_rate(const MechView &m, const double *
   double phi = M;
   if (meta_type(meta) == 2) {
     const double dlnkf = m.b[i] * invT + m.Th[i] * invT * invT;
-    phi = troe_factor<false>(m.troe + NTROE * meta_troe(meta), T, logT, invT, kf, dlnkf, M,
+    phi = troe_factor<false>(m.troe + NTROE * meta_troe(meta), T, logT, invT, lnkf, dlnkf, M,
                              m.etab).P;
   }
   return phi * (kf * fwd - kr * rev);
@@ -347,7 +348,8 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
     const int meta = m.meta[i];
     const int *sl = m.slot + 6 * i;
     const int nre = meta_nreac(meta), npr = meta_nprod(meta), type = meta_type(meta);
-    const double kf = kexp(m.lnA[i] + m.b[i] * logT - m.Th[i] * invT, m.etab);
+    const double lnkf = m.lnA[i] + m.b[i] * logT - m.Th[i] * invT;
+    const double kf = kexp(lnkf, m.etab);
     double lnKc = m.dnu[i] * lnPf, dH = 0.0, fwd = 1.0, rev = 1.0;
     for (int s = 0; s < nre; ++s) {
       lnKc -= b.g[sl[s]];
@@ -370,8 +372,8 @@ __device__ __noinline__ int warp_chem(const MechView &m, const WarpBuf<LT> &b, d
         dphi_dM = 1.0;
       } else {
         const double *tp = m.troe + NTROE * meta_troe(meta);
-        TroeOut t = wantJ ? troe_factor<true>(tp, T, logT, invT, kf, dlnkf, M, m.etab)
-                          : troe_factor<false>(tp, T, logT, invT, kf, dlnkf, M, m.etab);
+        TroeOut t = wantJ ? troe_factor<true>(tp, T, logT, invT, lnkf, dlnkf, M, m.etab)
+                          : troe_factor<false>(tp, T, logT, invT, lnkf, dlnkf, M, m.etab);
         phi = t.P;
         dphi_dT = t.P * t.dlnP_dT;
         dphi_dM = t.P * t.dlnP_dM;
