@@ -556,15 +556,31 @@ __device__ __forceinline__ void cdiv(LT a, LT b, LT c, LT d, LT &re, LT &im) {
   }
 }
 
+// Complex matrices of the thread layouts keep (re, im) interleaved, so an
+// entry is one 8-byte (FP32) or 16-byte (FP64) access.
 template <typename LT>
-__device__ __noinline__ int lu_cplx(int n, LT *ar, LT *ai, int *ip) {
+struct CplxOf;
+template <>
+struct CplxOf<float> {
+  using type = float2;
+};
+template <>
+struct CplxOf<double> {
+  using type = double2;
+};
+template <typename LT>
+using cplx_t = typename CplxOf<LT>::type;
+
+template <typename LT>
+__device__ __noinline__ int lu_cplx(int n, cplx_t<LT> *a, int *ip) {
   #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     int p = k;
-    LT amax = fabs(ar[k * n + k]) + fabs(ai[k * n + k]);
+    LT amax = fabs(a[k * n + k].x) + fabs(a[k * n + k].y);
     #pragma unroll 1
     for (int i = k + 1; i < n; ++i) {
-      LT v = fabs(ar[i * n + k]) + fabs(ai[i * n + k]);
+      const cplx_t<LT> e = a[i * n + k];
+      LT v = fabs(e.x) + fabs(e.y);
       if (v > amax) {
         amax = v;
         p = i;
@@ -575,26 +591,25 @@ __device__ __noinline__ int lu_cplx(int n, LT *ar, LT *ai, int *ip) {
     if (p != k)
       #pragma unroll 1
       for (int j = 0; j < n; ++j) {
-        LT t = ar[k * n + j];
-        ar[k * n + j] = ar[p * n + j];
-        ar[p * n + j] = t;
-        t = ai[k * n + j];
-        ai[k * n + j] = ai[p * n + j];
-        ai[p * n + j] = t;
+        const cplx_t<LT> t = a[k * n + j];
+        a[k * n + j] = a[p * n + j];
+        a[p * n + j] = t;
       }
-    const LT pr = ar[k * n + k], pi = ai[k * n + k];
+    const cplx_t<LT> pk = a[k * n + k];
     #pragma unroll 1
     for (int i = k + 1; i < n; ++i) {
       LT lr, li;
-      cdiv(ar[i * n + k], ai[i * n + k], pr, pi, lr, li);
-      ar[i * n + k] = lr;
-      ai[i * n + k] = li;
+      cdiv(a[i * n + k].x, a[i * n + k].y, pk.x, pk.y, lr, li);
+      a[i * n + k].x = lr;
+      a[i * n + k].y = li;
       if (lr != LT(0) || li != LT(0))
         #pragma unroll 1
         for (int j = k + 1; j < n; ++j) {
-          LT ur = ar[k * n + j], ui = ai[k * n + j];
-          ar[i * n + j] -= lr * ur - li * ui;
-          ai[i * n + j] -= lr * ui + li * ur;
+          const cplx_t<LT> u = a[k * n + j];
+          cplx_t<LT> e = a[i * n + j];
+          e.x -= lr * u.x - li * u.y;
+          e.y -= lr * u.y + li * u.x;
+          a[i * n + j] = e;
         }
     }
   }
@@ -602,56 +617,53 @@ __device__ __noinline__ int lu_cplx(int n, LT *ar, LT *ai, int *ip) {
 }
 
 template <int MAXN, typename LT, typename VT>
-__device__ __noinline__ void lu_solve_cplx(int n, const LT *lr, const LT *li, const int *ip, VT *br,
+__device__ __noinline__ void lu_solve_cplx(int n, const cplx_t<LT> *l, const int *ip, VT *br,
                                            VT *bi) {
-  LT vr[MAXN], vi[MAXN];
+  cplx_t<LT> v[MAXN];
   #pragma unroll 1
   for (int k = 0; k < n; ++k) {
-    vr[k] = LT(br[k]);
-    vi[k] = LT(bi[k]);
+    v[k].x = LT(br[k]);
+    v[k].y = LT(bi[k]);
   }
   #pragma unroll 1
   for (int k = 0; k < n; ++k) {
     const int p = ip[k];
     if (p != k) {
-      LT t = vr[k];
-      vr[k] = vr[p];
-      vr[p] = t;
-      t = vi[k];
-      vi[k] = vi[p];
-      vi[p] = t;
+      const cplx_t<LT> t = v[k];
+      v[k] = v[p];
+      v[p] = t;
     }
   }
   #pragma unroll 1
   for (int i = 1; i < n; ++i) {
-    LT sr = vr[i], si = vi[i];
+    LT sr = v[i].x, si = v[i].y;
     #pragma unroll 1
     for (int j = 0; j < i; ++j) {
-      const LT xr = vr[j], xi = vi[j];
-      sr -= lr[i * n + j] * xr - li[i * n + j] * xi;
-      si -= lr[i * n + j] * xi + li[i * n + j] * xr;
+      const cplx_t<LT> x = v[j], m = l[i * n + j];
+      sr -= m.x * x.x - m.y * x.y;
+      si -= m.x * x.y + m.y * x.x;
     }
-    vr[i] = sr;
-    vi[i] = si;
+    v[i].x = sr;
+    v[i].y = si;
   }
   #pragma unroll 1
   for (int i = n - 1; i >= 0; --i) {
-    LT sr = vr[i], si = vi[i];
+    LT sr = v[i].x, si = v[i].y;
     #pragma unroll 1
     for (int j = i + 1; j < n; ++j) {
-      const LT xr = vr[j], xi = vi[j];
-      sr -= lr[i * n + j] * xr - li[i * n + j] * xi;
-      si -= lr[i * n + j] * xi + li[i * n + j] * xr;
+      const cplx_t<LT> x = v[j], m = l[i * n + j];
+      sr -= m.x * x.x - m.y * x.y;
+      si -= m.x * x.y + m.y * x.x;
     }
     LT qr, qi;
-    cdiv(sr, si, lr[i * n + i], li[i * n + i], qr, qi);
-    vr[i] = qr;
-    vi[i] = qi;
+    cdiv(sr, si, l[i * n + i].x, l[i * n + i].y, qr, qi);
+    v[i].x = qr;
+    v[i].y = qi;
   }
   #pragma unroll 1
   for (int k = 0; k < n; ++k) {
-    br[k] = VT(vr[k]);
-    bi[k] = VT(vi[k]);
+    br[k] = VT(v[k].x);
+    bi[k] = VT(v[k].y);
   }
 }
 

@@ -72,7 +72,8 @@ struct Work {
   double a1[MAXN], a2[MAXN], a3[MAXN];
   double u[MAXN], fu[MAXN], F1[MAXN], F2[MAXN], fe[MAXN];
   LT J[MAXN * MAXN];  // the Jacobian is stored (and assembled) in the matrix type
-  LT E1[MAXN * MAXN], E2r[MAXN * MAXN], E2i[MAXN * MAXN];
+  LT E1[MAXN * MAXN];
+  cplx_t<LT> E2[MAXN * MAXN];  // (alpha + i beta)/h I - J, (re, im) interleaved
   int ip1[MAXN], ip2[MAXN];
   WorkChem<MAXN> cs;
   JacScratch<MAXN, LT> js;
@@ -115,18 +116,18 @@ __device__ int factor(int N, Work<MAXN, LT> &w, double h) {
   #pragma unroll 1
   for (int q = 0; q < N * N; ++q) {
     w.E1[q] = -w.J[q];
-    w.E2r[q] = -w.J[q];
-    w.E2i[q] = LT(0);
+    w.E2[q].x = -w.J[q];
+    w.E2[q].y = LT(0);
   }
   #pragma unroll 1
   for (int i = 0; i < N; ++i) {
     w.E1[i * N + i] = LT(fac1) - w.J[i * N + i];
-    w.E2r[i * N + i] = LT(alphn) - w.J[i * N + i];
-    w.E2i[i * N + i] = LT(betan);
+    w.E2[i * N + i].x = LT(alphn) - w.J[i * N + i];
+    w.E2[i * N + i].y = LT(betan);
   }
   int s1 = lu_real<LT>(N, w.E1, w.ip1);
   if (s1) return s1;
-  return lu_cplx<LT>(N, w.E2r, w.E2i, w.ip2);
+  return lu_cplx<LT>(N, w.E2, w.ip2);
 }
 
 // Starting values: zero (or the supplied guess) on the first step, else the
@@ -183,7 +184,7 @@ __device__ double newton_correction(int N, Work<MAXN, LT> &w, double h, const do
     w.z3[i] = g3 - (betan * w.w2[i] + alphn * w.w3[i]);
   }
   lu_solve_real<MAXN, LT, double>(N, w.E1, w.ip1, w.z1);
-  lu_solve_cplx<MAXN, LT, double>(N, w.E2r, w.E2i, w.ip2, w.z2, w.z3);
+  lu_solve_cplx<MAXN, LT, double>(N, w.E2, w.ip2, w.z2, w.z3);
   double sum = 0.0;
   #pragma unroll 1
   for (int i = 0; i < N; ++i) {
